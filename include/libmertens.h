@@ -1,0 +1,202 @@
+/*
+ * libmertens -- exact isolated values of the Mertens function on one GB300.
+ *
+ * The method is the one of "Computing the Mertens function on a GPU"
+ * (arXiv:1108.0135), Sec. 2-3: pick a sieve limit u > sqrt(n), keep an array
+ * of X = floor(n/u) entries that end up holding M(floor(n/x)), x = 1..X, sieve
+ * M(y) for y < u block by block, add every block's contributions to the array,
+ * and resolve the array at the end.  M(y) = sum_{m <= y} mu(m) (Sec. 1).
+ *
+ * All entry points are plain C.  Pointers are host pointers unless the
+ * argument name ends in _dev (device memory of the current CUDA device).
+ * `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ * stream).  Every function returns an int status (MERTENS_OK = 0 or one of the
+ * codes below); nothing aborts, throws or traps on the device.  Results are
+ * exact integers: there is no tolerance anywhere in this library.
+ *
+ * Thread safety: distinct plans may be used from distinct host threads; one
+ * plan must not be used from two threads at once.
+ */
+#ifndef LIBMERTENS_H
+#define LIBMERTENS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define MERTENS_OK 0
+#define MERTENS_EINVAL 1    /* an argument is out of range (see each call)  */
+#define MERTENS_ENOMEM 2    /* a device or host allocation failed           */
+#define MERTENS_ECUDA 3     /* a CUDA runtime call failed                   */
+#define MERTENS_ETIMEOUT 4  /* a bounded device wait expired                */
+#define MERTENS_ENOTREADY 5 /* result asked for before mertens_run          */
+#define MERTENS_ENOTSUP 6   /* input outside what this build supports       */
+#define MERTENS_EOVERFLOW 7 /* a value left its integer type (see notes)    */
+
+/* Unsigned 128-bit integer as two 64-bit words: value = hi * 2^64 + lo. */
+typedef struct {
+    uint64_t lo, hi;
+} mertens_u128;
+
+/* Opaque plan: the targets, their arrays and every device buffer. */
+typedef struct mertens_plan_s *mertens_plan_t;
+
+/* Human-readable text for a status code (static storage, never NULL). */
+const char *mertens_strerror(int code);
+
+/* Text of the last error raised on this host thread (static per thread). */
+const char *mertens_last_error(void);
+
+/*
+ * Device-memory hook.  By default the library allocates with cudaMalloc and
+ * frees with cudaFree.  A caller (for example a PyTorch process that wants
+ * the caching allocator) may install its own pair; `ctx` is passed back
+ * unchanged.  alloc must return 256-byte aligned device memory or NULL.
+ * Passing alloc = NULL restores the default.  Applies to plans created after
+ * the call; each plan frees with the pair it allocated with.
+ */
+typedef void *(*mertens_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*mertens_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
+int mertens_set_allocator(mertens_alloc_fn alloc, mertens_free_fn release, void *ctx);
+
+/*
+ * mertens_plan -- prepare the computation of M(n_i), i < count, with one
+ * shared sieve pass (Sec. 2: "if we want to compute M(x) for multiple close
+ * values of x, we only need to do sieving once").
+ *
+ *   out        receives the plan (owned by the caller; free with
+ *              mertens_destroy).
+ *   n          `count` targets, each 1 <= n_i < 2^63 in this build
+ *              (MERTENS_ENOTSUP at or above 2^63).  Copied; the caller keeps
+ *              ownership.
+ *   u          sieve limit shared by all targets.  {0,0} = chosen per target
+ *              by the library (about 0.9 * n_i^(2/3)).  Otherwise it must
+ *              satisfy floor(sqrt(n_i)) < u <= n_i for every i (u = 1 is
+ *              allowed for n_i = 1), else MERTENS_EINVAL.  Each target's array
+ *              has X_i = floor(n_i/u_i) entries (Sec. 2).
+ *   block_len  length of a sieve block in y (Sec. 3, "divide calculations
+ *              into blocks of y"); 0 = chosen by the library.  Any value >= 1
+ *              is honoured exactly.
+ *
+ * Allocates all device memory of the plan on the current device (through the
+ * hook above).  Host-side work only otherwise; no kernel is launched.
+ * Errors: MERTENS_EINVAL (count = 0, bad n or u), MERTENS_ENOTSUP,
+ * MERTENS_ENOMEM, MERTENS_ECUDA.  On error *out is set to NULL.
+ */
+int mertens_plan(mertens_plan_t *out, const mertens_u128 *n, size_t count,
+                 mertens_u128 u, uint64_t block_len);
+
+/*
+ * mertens_run -- enqueue the whole computation on `stream`: for every sieve
+ * block, mu_sieve (segmented Moebius sieve, Sec. 3), m_scan (M(y) by prefix
+ * sum with the carry of the previous block), mertens_update (every array
+ * entry's contributions from the block, Sec. 2-3); then resolve (Sec. 2, "it
+ * is a simple task to compute final values of M").  Returns once everything
+ * is enqueued; the work runs asynchronously.  May be called again on the same
+ * plan (the arrays are reset first).  Errors: MERTENS_EINVAL (NULL plan),
+ * MERTENS_ECUDA (a launch failed).
+ */
+int mertens_run(mertens_plan_t plan, void *stream);
+
+/*
+ * mertens_result -- wait for the last mertens_run of `plan`, then return
+ * target i's results.
+ *   M_n      receives M(n_i) (may be NULL).
+ *   entries  NULL, or a host buffer of `cap` int64 that receives
+ *            M(floor(n_i/x)) for x = 1..min(cap, X_i) -- the paper's array,
+ *            "all values of M(y) for y = floor(n/c)" (Sec. 1-2).
+ *   len      receives X_i (may be NULL).
+ * Values are exact; they are computed mod 2^64 and read as int64, which is
+ * exact while |M| < 2^63.  Errors: MERTENS_EINVAL (bad i), MERTENS_ENOTREADY
+ * (no run yet), MERTENS_ETIMEOUT (a bounded device wait gave up),
+ * MERTENS_EOVERFLOW (some |M(y)| of the sieve did not fit the M(y) block
+ * type), MERTENS_ECUDA.
+ */
+int mertens_result(mertens_plan_t plan, size_t i, int64_t *M_n, int64_t *entries,
+                   size_t cap, size_t *len);
+
+/* Frees every buffer of the plan (after waiting for its last run). NULL ok. */
+void mertens_destroy(mertens_plan_t plan);
+
+/* ---- host-only planning queries (no GPU needed) ------------------------- */
+
+/* Per-target shape of a plan or of a would-be plan. */
+typedef struct {
+    mertens_u128 n;          /* target                                      */
+    mertens_u128 u;          /* sieve limit used                            */
+    uint64_t X;              /* array length floor(n/u) (Sec. 2)            */
+    uint64_t y_max;          /* largest y whose M(y) the update reads       */
+    uint64_t direct_terms;   /* sum over x of floor(sqrt(floor(n/x)))       */
+    uint64_t gathered_terms; /* sum over x of the j-range of gathered terms */
+} mertens_query_info;
+
+/*
+ * mertens_describe -- fill `info` for target n with sieve limit u ({0,0} =
+ * the library's choice), without touching the GPU.  The term counts are the
+ * closed forms of the update's work (Sec. 2): entry x with k = floor(n/x) and
+ * s = floor(sqrt(k)) has s direct terms M(y)(floor(k/y) - floor(k/(y+1))),
+ * y = 1..s, and floor(k/(s+1)) - floor(k/u) gathered terms M(floor(k/j)),
+ * j = floor(k/u)+1 .. floor(k/(s+1)).  Errors: MERTENS_EINVAL, MERTENS_ENOTSUP.
+ */
+int mertens_describe(mertens_u128 n, mertens_u128 u, mertens_query_info *info);
+
+/* mertens_plan_info -- the same record for target i of an existing plan. */
+int mertens_plan_info(mertens_plan_t plan, size_t i, mertens_query_info *info);
+
+/* Run statistics.  Phase times are CUDA-event device times averaged over the
+ * runs made since profiling was last enabled (0 when profiling is off). */
+typedef struct {
+    double total_ms;      /* whole run, first kernel to last               */
+    double sieve_ms;      /* a1 mu_sieve, all blocks                        */
+    double scan_ms;       /* a2 m_scan (tile carries + M(y)), all blocks    */
+    double update_ms;     /* a3 mertens_update = dense + gathered           */
+    double dense_ms;      /*    dense part (squarefree list + mu-form sums) */
+    double gather_ms;     /*    gathered part, all blocks                   */
+    double resolve_ms;    /* a4 resolve                                     */
+    uint64_t runs;        /* runs averaged                                  */
+    uint64_t blocks;      /* sieve blocks                                   */
+    uint64_t y_sieved;    /* y values sieved                                */
+    uint64_t terms;       /* direct + gathered update terms, all targets    */
+    uint64_t kernels;     /* kernel launches of the last run                */
+    uint64_t h2d_bytes;   /* host-to-device bytes of the plan's inputs      */
+    uint64_t d2h_bytes;   /* device-to-host bytes read by mertens_result
+                             since the last mertens_run                     */
+} mertens_run_stats;
+
+/* Enables (1) or disables (0) per-phase events for later runs of `plan`
+ * and clears the runs recorded so far (off by default; the events add
+ * records to the stream but serialise nothing). */
+int mertens_plan_set_profiling(mertens_plan_t plan, int enable);
+
+/* Waits for the last run and fills `stats`. */
+int mertens_run_stats_get(mertens_plan_t plan, mertens_run_stats *stats);
+
+/* ---- step-level entry points (one step of the path on device buffers) --- */
+
+/*
+ * mertens_sieve_mu -- step a1 alone: mu(y) for y = y1 .. y1+len-1 into
+ * mu_dev[0..len) (int8), by the segmented log sieve (Sec. 3) with an exact
+ * decision rule.  1 <= y1, y1+len-1 < 2^63, len <= 2^31.  Scratch is taken
+ * from the allocator hook and freed before return (the call synchronises
+ * `stream`).  Errors: MERTENS_EINVAL, MERTENS_ENOMEM, MERTENS_ECUDA.
+ */
+int mertens_sieve_mu(uint64_t y1, uint64_t len, int8_t *mu_dev, void *stream);
+
+/*
+ * mertens_sieve_M -- steps a1+a2: M(y) for y = y1 .. y1+len-1 into
+ * M_dev[0..len) (int32), given carry = M(y1-1) (Sec. 3, step 5: "add up all
+ * values of mu(y)").  Same limits and scratch rule as mertens_sieve_mu.
+ * MERTENS_EOVERFLOW if some |M(y)| >= 2^31.
+ */
+int mertens_sieve_M(uint64_t y1, uint64_t len, int64_t carry, int32_t *M_dev,
+                    void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LIBMERTENS_H */

@@ -1,0 +1,15 @@
+"""libmertens: exact isolated values of the Mertens function on one GB300.
+
+The computation (arXiv:1108.0135, Sec. 2-3) runs entirely in the CUDA library
+``_build/libmertens.so`` (sources under ``csrc/``, interface in
+``include/libmertens.h``).  This package is its thin ctypes binding: the
+functions below have the C names and only marshal arguments.
+"""
+from ._lib import (  # noqa: F401
+    EXPORTS, MERTENS_EINVAL, MERTENS_ENOMEM, MERTENS_ENOTREADY, MERTENS_ENOTSUP, MERTENS_EOVERFLOW,
+    MERTENS_ETIMEOUT, MERTENS_OK, MertensError, load, mertens, mertens_describe, mertens_destroy,
+    mertens_last_error, mertens_plan, mertens_plan_info, mertens_plan_set_profiling,
+    mertens_result, mertens_result_into, mertens_run, mertens_run_stats_get,
+    mertens_set_allocator, mertens_sieve_M, mertens_sieve_mu, mertens_strerror,
+    use_torch_allocator,
+)

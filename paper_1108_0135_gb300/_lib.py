@@ -1,0 +1,291 @@
+"""ctypes binding of libmertens (include/libmertens.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Device buffers may be given as torch tensors or raw integer device
+pointers; streams as torch.cuda.Stream, raw handles or None.  There is no CPU
+fallback: if the library cannot be built or loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+MERTENS_OK = 0
+MERTENS_EINVAL = 1
+MERTENS_ENOMEM = 2
+MERTENS_ECUDA = 3
+MERTENS_ETIMEOUT = 4
+MERTENS_ENOTREADY = 5
+MERTENS_ENOTSUP = 6
+MERTENS_EOVERFLOW = 7
+
+
+class mertens_u128(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_uint64), ("hi", ctypes.c_uint64)]
+
+
+class mertens_query_info(ctypes.Structure):
+    _fields_ = [("n", mertens_u128), ("u", mertens_u128), ("X", ctypes.c_uint64),
+                ("y_max", ctypes.c_uint64), ("direct_terms", ctypes.c_uint64),
+                ("gathered_terms", ctypes.c_uint64)]
+
+
+class mertens_run_stats(ctypes.Structure):
+    _fields_ = [("total_ms", ctypes.c_double), ("sieve_ms", ctypes.c_double),
+                ("scan_ms", ctypes.c_double), ("update_ms", ctypes.c_double),
+                ("dense_ms", ctypes.c_double), ("gather_ms", ctypes.c_double),
+                ("resolve_ms", ctypes.c_double), ("runs", ctypes.c_uint64),
+                ("blocks", ctypes.c_uint64), ("y_sieved", ctypes.c_uint64),
+                ("terms", ctypes.c_uint64), ("kernels", ctypes.c_uint64),
+                ("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                           ctypes.c_void_p)
+
+# Every symbol include/libmertens.h declares.
+EXPORTS = [
+    "mertens_strerror", "mertens_last_error", "mertens_set_allocator", "mertens_plan",
+    "mertens_run", "mertens_result", "mertens_destroy", "mertens_describe",
+    "mertens_plan_info", "mertens_plan_set_profiling", "mertens_run_stats_get",
+    "mertens_sieve_mu", "mertens_sieve_M",
+]
+
+_lock = threading.Lock()
+_lib = None
+
+
+class MertensError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str):
+        self.code = code
+        super().__init__(f"{where}: {detail} (status {code})")
+
+
+def load():
+    """Builds (if stale) and loads libmertens.so; raises if that fails."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build()
+        lib = ctypes.CDLL(path)
+        P = ctypes.c_void_p
+        u64, i64, sz, c_int = ctypes.c_uint64, ctypes.c_int64, ctypes.c_size_t, ctypes.c_int
+        lib.mertens_strerror.argtypes = [c_int]
+        lib.mertens_strerror.restype = ctypes.c_char_p
+        lib.mertens_last_error.argtypes = []
+        lib.mertens_last_error.restype = ctypes.c_char_p
+        lib.mertens_set_allocator.argtypes = [ALLOC_FN, FREE_FN, P]
+        lib.mertens_set_allocator.restype = c_int
+        lib.mertens_plan.argtypes = [ctypes.POINTER(P), ctypes.POINTER(mertens_u128), sz,
+                                     mertens_u128, u64]
+        lib.mertens_plan.restype = c_int
+        lib.mertens_run.argtypes = [P, P]
+        lib.mertens_run.restype = c_int
+        lib.mertens_result.argtypes = [P, sz, ctypes.POINTER(i64), P, sz,
+                                       ctypes.POINTER(sz)]
+        lib.mertens_result.restype = c_int
+        lib.mertens_destroy.argtypes = [P]
+        lib.mertens_destroy.restype = None
+        lib.mertens_describe.argtypes = [mertens_u128, mertens_u128,
+                                         ctypes.POINTER(mertens_query_info)]
+        lib.mertens_describe.restype = c_int
+        lib.mertens_plan_info.argtypes = [P, sz, ctypes.POINTER(mertens_query_info)]
+        lib.mertens_plan_info.restype = c_int
+        lib.mertens_plan_set_profiling.argtypes = [P, c_int]
+        lib.mertens_plan_set_profiling.restype = c_int
+        lib.mertens_run_stats_get.argtypes = [P, ctypes.POINTER(mertens_run_stats)]
+        lib.mertens_run_stats_get.restype = c_int
+        lib.mertens_sieve_mu.argtypes = [u64, u64, P, P]
+        lib.mertens_sieve_mu.restype = c_int
+        lib.mertens_sieve_M.argtypes = [u64, u64, i64, P, P]
+        lib.mertens_sieve_M.restype = c_int
+        _lib = lib
+        return lib
+
+
+def _check(rc: int, where: str):
+    if rc != MERTENS_OK:
+        lib = load()
+        detail = lib.mertens_last_error().decode() or lib.mertens_strerror(rc).decode()
+        raise MertensError(rc, where, detail)
+
+
+def u128(v: int) -> mertens_u128:
+    v = int(v)
+    if v < 0 or v >= 1 << 128:
+        raise ValueError("value out of the unsigned 128-bit range")
+    return mertens_u128(v & ((1 << 64) - 1), v >> 64)
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    raise TypeError("expected a torch tensor or an integer device pointer")
+
+
+def _stream(s) -> int:
+    if s is None:
+        return 0
+    if isinstance(s, int):
+        return s
+    if hasattr(s, "cuda_stream"):
+        return int(s.cuda_stream)
+    raise TypeError("expected a torch.cuda.Stream, a raw handle or None")
+
+
+# ---- the C-ABI calls, same names ------------------------------------------
+
+def mertens_strerror(code: int) -> str:
+    return load().mertens_strerror(code).decode()
+
+
+def mertens_last_error() -> str:
+    return load().mertens_last_error().decode()
+
+
+def mertens_plan(n, u: int = 0, block_len: int = 0) -> int:
+    """Returns an opaque plan handle for the targets n (int or list of ints)."""
+    lib = load()
+    ns = [int(n)] if isinstance(n, (int, np.integer)) else [int(v) for v in n]
+    arr = (mertens_u128 * len(ns))(*[u128(v) for v in ns])
+    h = ctypes.c_void_p()
+    _check(lib.mertens_plan(ctypes.byref(h), arr, len(ns), u128(u), int(block_len)),
+           "mertens_plan")
+    return int(h.value)
+
+
+def mertens_run(plan: int, stream=None) -> None:
+    _check(load().mertens_run(plan, _stream(stream)), "mertens_run")
+
+
+def mertens_result(plan: int, i: int = 0, entries: bool = False, cap: int | None = None):
+    """(M(n_i), array or None): the array holds M(floor(n_i/x)) for x = 1..X_i."""
+    lib = load()
+    m = ctypes.c_int64()
+    ln = ctypes.c_size_t()
+    if entries:
+        info = mertens_plan_info(plan, i)
+        cnt = info["X"] if cap is None else min(cap, info["X"])
+        out = np.zeros(cnt, dtype=np.int64)
+        _check(lib.mertens_result(plan, i, ctypes.byref(m), out.ctypes.data, cnt,
+                                  ctypes.byref(ln)), "mertens_result")
+        return int(m.value), out
+    _check(lib.mertens_result(plan, i, ctypes.byref(m), None, 0, ctypes.byref(ln)),
+           "mertens_result")
+    return int(m.value), None
+
+
+def mertens_result_into(plan: int, i: int, out: np.ndarray) -> int:
+    """Copies target i's array into the host buffer `out` (int64); returns M(n_i)."""
+    lib = load()
+    m = ctypes.c_int64()
+    ln = ctypes.c_size_t()
+    _check(lib.mertens_result(plan, i, ctypes.byref(m), out.ctypes.data, out.size,
+                              ctypes.byref(ln)), "mertens_result")
+    return int(m.value)
+
+
+def mertens_destroy(plan: int) -> None:
+    if plan:
+        load().mertens_destroy(plan)
+
+
+def _info_dict(info: mertens_query_info) -> dict:
+    return dict(n=info.n.lo | (info.n.hi << 64), u=info.u.lo | (info.u.hi << 64), X=info.X,
+                y_max=info.y_max, direct_terms=info.direct_terms,
+                gathered_terms=info.gathered_terms)
+
+
+def mertens_describe(n: int, u: int = 0) -> dict:
+    info = mertens_query_info()
+    _check(load().mertens_describe(u128(n), u128(u), ctypes.byref(info)), "mertens_describe")
+    return _info_dict(info)
+
+
+def mertens_plan_info(plan: int, i: int = 0) -> dict:
+    info = mertens_query_info()
+    _check(load().mertens_plan_info(plan, i, ctypes.byref(info)), "mertens_plan_info")
+    return _info_dict(info)
+
+
+def mertens_plan_set_profiling(plan: int, enable: bool = True) -> None:
+    _check(load().mertens_plan_set_profiling(plan, 1 if enable else 0),
+           "mertens_plan_set_profiling")
+
+
+def mertens_run_stats_get(plan: int) -> dict:
+    st = mertens_run_stats()
+    _check(load().mertens_run_stats_get(plan, ctypes.byref(st)), "mertens_run_stats_get")
+    return {name: getattr(st, name) for name, _ in mertens_run_stats._fields_}
+
+
+def mertens_sieve_mu(y1: int, length: int, mu_dev, stream=None) -> None:
+    _check(load().mertens_sieve_mu(int(y1), int(length), _ptr(mu_dev), _stream(stream)),
+           "mertens_sieve_mu")
+
+
+def mertens_sieve_M(y1: int, length: int, carry: int, M_dev, stream=None) -> None:
+    _check(load().mertens_sieve_M(int(y1), int(length), int(carry), _ptr(M_dev),
+                                  _stream(stream)), "mertens_sieve_M")
+
+
+_alloc_keepalive = []
+
+
+def mertens_set_allocator(alloc=None, release=None, ctx=None) -> None:
+    """Installs a device-memory hook (ctypes callbacks) or, with no argument,
+    restores cudaMalloc/cudaFree."""
+    lib = load()
+    if alloc is None:
+        _check(lib.mertens_set_allocator(ALLOC_FN(), FREE_FN(), None), "mertens_set_allocator")
+        _alloc_keepalive.clear()
+        return
+    a, r = ALLOC_FN(alloc), FREE_FN(release)
+    _alloc_keepalive[:] = [a, r]
+    _check(lib.mertens_set_allocator(a, r, ctx), "mertens_set_allocator")
+
+
+def use_torch_allocator() -> None:
+    """Routes the library's device allocations through PyTorch's caching
+    allocator on the current device."""
+    import torch
+
+    def _alloc(nbytes, stream, ctx):
+        dev = torch.cuda.current_device()
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream or 0))
+        except RuntimeError:
+            return 0
+
+    def _free(ptr, nbytes, stream, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    mertens_set_allocator(_alloc, _free)
+
+
+# ---- convenience ----------------------------------------------------------
+
+def mertens(n, u: int = 0, block_len: int = 0, entries: bool = False, stream=None):
+    """M(n) (or M(n_i) for a list, one shared sieve pass), computed on the GPU.
+
+    With entries=True each result is (M(n_i), array of M(floor(n_i/x)))."""
+    single = isinstance(n, (int, np.integer))
+    ns = [int(n)] if single else [int(v) for v in n]
+    plan = mertens_plan(ns, u, block_len)
+    try:
+        mertens_run(plan, stream)
+        out = [mertens_result(plan, i, entries) for i in range(len(ns))]
+    finally:
+        mertens_destroy(plan)
+    res = [o if entries else o[0] for o in out]
+    return res[0] if single else res

@@ -1,0 +1,143 @@
+// Device helpers shared by the libmertens kernels (sm_103a).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mert {
+
+// Sieve tile: y values per CTA tile of mu_sieve / m_scan (32-bit smem words).
+constexpr int kSieveTile = 32768;
+constexpr int kSieveThreads = 1024;
+// Dense chunk: y values per chunk of the squarefree list used by the dense
+// update, and the largest number of squarefree y a chunk can hold (one y in
+// four is a multiple of 4, so at most 3/4 of any 4096 consecutive y).
+constexpr int kChunk = 4096;
+constexpr int kChunkCap = 3072;
+// Gathered terms per warp work item.
+constexpr int kSparseItem = 1024;
+
+// Fixed-point scale of the log sieve: lg(p) = round(16 * log2 p).
+constexpr int kLogScale = 16;
+// Word layout of the log sieve: bits 0..10 sum of lg(p), bits 11..15 number
+// of distinct sieving primes, bits 16..31 number of sieving-prime squares.
+constexpr uint32_t kCountOne = 1u << 11;
+constexpr uint32_t kSquareOne = 1u << 16;
+// Pre-sieve pattern: primes 2,3,5,7 and their squares, period 4*9*25*49.
+constexpr uint32_t kPatternPeriod = 44100;
+
+// Error bits of the plan's device status word.
+constexpr uint32_t kErrMOverflow = 1u;   // |M(y)| did not fit int32
+constexpr uint32_t kErrBadIndex = 2u;    // a self-check found an index out of range
+
+// Bit length of v (0 for v = 0).
+__host__ __device__ __forceinline__ unsigned bitlen64(uint64_t v)
+{
+#ifdef __CUDA_ARCH__
+    return 64u - (unsigned)__clzll((long long)v);
+#else
+    return v ? 64u - (unsigned)__builtin_clzll(v) : 0u;
+#endif
+}
+
+// Division by an invariant divisor d (Granlund & Montgomery, "Division by
+// invariant integers using multiplication", PLDI 1994, Sec. 4): with
+// l = ceil(log2 d) and m = floor(2^(63+l)/d) + 1 (so m < 2^64), every k < 2^63
+// has floor(k/d) = floor(m*k / 2^(63+l)) = floor(mulhi64(m, 2k) / 2^l).
+__host__ __device__ __forceinline__ unsigned magic_shift(uint64_t d)
+{
+    return bitlen64(d - 1);
+}
+
+// m = floor(2^(63+l)/d) + 1 by restoring long division of the 128-bit
+// numerator 2^(63+l) (high word 2^(l-1), low word 0) by d; the high word is
+// below d, so the quotient fits 64 bits.  d = 1 gives 2^63 + 1.
+__host__ __device__ inline uint64_t magic_of(uint64_t d)
+{
+    unsigned l = magic_shift(d);
+    if (l == 0)
+        return (1ull << 63) + 1ull;
+    uint64_t r = 1ull << (l - 1);  // running remainder, always < d
+    uint64_t q = 0;
+    for (int i = 63; i >= 0; --i) {
+        // r = 2r (next numerator bit is 0); r < 2d < 2^39, no overflow
+        r <<= 1;
+        q <<= 1;
+        if (r >= d) {
+            r -= d;
+            q |= 1ull;
+        }
+    }
+    return q + 1ull;
+}
+
+__device__ __forceinline__ uint64_t div_magic(uint64_t k2, uint64_t m, unsigned l)
+{
+    return __umul64hi(k2, m) >> l;
+}
+
+// Warp-wide sum of a 64-bit value (mod 2^64).
+__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ int64_t warp_sum_i64(int64_t v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// Block-wide scans (warp shuffles, then a pass over the warp totals).
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T n = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o)
+            v += n;
+    }
+    return v;
+}
+
+// Exclusive scan over the CTA; returns the thread's exclusive prefix and
+// writes the CTA total to *total.  `sh` holds 33 values of T.
+template <typename T>
+__device__ __forceinline__ T block_excl_scan(T v, T *sh, T *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    T inc = warp_incl_scan(v);
+    if (lane == 31)
+        sh[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        T w = lane < nw ? sh[lane] : T(0);
+        T wi = warp_incl_scan(w);
+        if (lane < nw)
+            sh[lane] = wi - w;
+        if (lane == nw - 1)
+            sh[32] = wi;
+    }
+    __syncthreads();
+    T res = sh[warp] + inc - v;
+    *total = sh[32];
+    __syncthreads();
+    return res;
+}
+
+__device__ __forceinline__ uint32_t block_scan_u32(uint32_t v, uint32_t *sh, uint32_t *total)
+{
+    return block_excl_scan<uint32_t>(v, sh, total);
+}
+
+}  // namespace mert

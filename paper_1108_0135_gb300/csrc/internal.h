@@ -1,0 +1,74 @@
+// Host-side declarations shared by the libmertens translation units.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/libmertens.h"
+
+namespace mert {
+
+// Device-memory hook captured by a plan (null alloc = cudaMalloc/cudaFree).
+struct Allocator {
+    mertens_alloc_fn alloc = nullptr;
+    mertens_free_fn release = nullptr;
+    void *ctx = nullptr;
+};
+Allocator current_allocator();
+void *dev_alloc(const Allocator &a, size_t bytes);
+void dev_free(const Allocator &a, void *p, size_t bytes);
+
+// Prime table of a plan (device arrays, index 0..np-1, primes ascending,
+// the first four are 2, 3, 5, 7 which the pre-sieve pattern covers).
+struct PrimeTable {
+    uint32_t np = 0;             // primes in the table
+    uint32_t *p = nullptr;       // prime
+    uint32_t *lg = nullptr;      // round(16 * log2 p)
+    uint64_t *m = nullptr;       // division magic of p
+    uint8_t *l = nullptr;        // division shift of p
+    uint32_t *blk_r = nullptr;   // per block: y1 mod p
+    uint32_t *blk_qm = nullptr;  // per block: floor(y1 / p) mod p
+    uint32_t *pattern = nullptr; // pre-sieve pattern, period 44100
+    // host copy of the primes (for counting primes <= a bound)
+    uint32_t *host_p = nullptr;
+    Allocator al;
+};
+
+// Arguments of one sieve block (steps a1 + a2).
+struct SieveLaunch {
+    uint64_t y1 = 0;          // first y of the block (>= 1)
+    uint64_t len = 0;         // y values in the block
+    int8_t *mu = nullptr;     // [len] mu output
+    int8_t *mu_aux = nullptr; // optional copy of mu for y <= aux_end, index y-1
+    uint64_t aux_end = 0;
+    int32_t *M = nullptr;     // [len] M output (nullptr = mu only)
+    int32_t *tile_sum = nullptr; // [tiles] scratch
+    int64_t *tile_off = nullptr; // [tiles] scratch
+    int64_t *carry = nullptr;    // device M(y1-1) in, M(y1+len-1) out
+    uint32_t *err = nullptr;     // device status word
+    cudaEvent_t mid = nullptr;   // if set: recorded after a1 ...
+    cudaEvent_t mid2 = nullptr;  // ... and this one before a2 (profiling)
+};
+
+// Builds the prime table for sieving up to y_max (host + device upload).
+int prime_table_create(PrimeTable *t, const Allocator &al, uint64_t y_max, cudaStream_t s);
+void prime_table_destroy(PrimeTable *t);
+// Number of primes in the table that are <= b.
+uint32_t prime_count_upto(const PrimeTable *t, uint64_t b);
+// Enqueues steps a1 (and a2 when L.M != nullptr) for one block.  Returns the
+// number of kernels launched, or -1 on a launch error.
+int sieve_block_enqueue(const PrimeTable *t, const SieveLaunch &L, cudaStream_t s);
+// Tiles of a block of `len` y values.
+inline uint64_t sieve_tiles(uint64_t len) { return (len + 32767) / 32768; }
+
+// Device-wide exclusive scan of n uint32 values into out[0..n] (out[n] =
+// total).  `scratch` holds at least scan_scratch_words(n) uint32.
+size_t scan_scratch_words(size_t n);
+int exclusive_scan_u32(const uint32_t *in, uint32_t *out, size_t n, uint32_t *scratch,
+                       cudaStream_t s);
+
+// Thread-local last-error text.
+void set_last_error(const char *fmt, ...);
+
+}  // namespace mert

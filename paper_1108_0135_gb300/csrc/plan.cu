@@ -1,0 +1,859 @@
+// libmertens C ABI: planning, the block loop of mertens_run, results.
+// The method is that of arXiv:1108.0135, Sec. 2-3; the kernels live in
+// sieve.cu (a1, a2) and update.cu (a3, a4).
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "../../include/libmertens.h"
+#include "common.cuh"
+#include "internal.h"
+#include "update.h"
+
+namespace mert {
+
+// ---------------------------------------------------------------------------
+// Errors and allocation.
+// ---------------------------------------------------------------------------
+static thread_local char g_last_error[512] = "";
+
+void set_last_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+    va_end(ap);
+}
+
+static std::mutex g_alloc_mu;
+static mertens_alloc_fn g_alloc = nullptr;
+static mertens_free_fn g_free = nullptr;
+static void *g_alloc_ctx = nullptr;
+
+Allocator current_allocator()
+{
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    Allocator a;
+    a.alloc = g_alloc;
+    a.release = g_free;
+    a.ctx = g_alloc_ctx;
+    return a;
+}
+
+void *dev_alloc(const Allocator &a, size_t bytes)
+{
+    if (bytes == 0)
+        bytes = 16;
+    if (a.alloc)
+        return a.alloc(bytes, nullptr, a.ctx);
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dev_free(const Allocator &a, void *p, size_t bytes)
+{
+    if (!p)
+        return;
+    if (a.alloc)
+        a.release(p, bytes, nullptr, a.ctx);
+    else
+        cudaFree(p);
+}
+
+static uint64_t isqrt64(uint64_t v)
+{
+    uint64_t r = (uint64_t)std::sqrt((double)v);
+    while (r > 0 && r > v / r)
+        --r;
+    while ((r + 1) <= v / (r + 1))
+        ++r;
+    return r;
+}
+
+}  // namespace mert
+
+using namespace mert;
+
+// ---------------------------------------------------------------------------
+// The plan.
+// ---------------------------------------------------------------------------
+// Phases of a run timed with CUDA events when profiling is on.
+enum { kPhSieve = 0, kPhScan = 1, kPhDense = 2, kPhGather = 3, kPhResolve = 4, kPhTotal = 5,
+       kPhases = 6 };
+
+struct PhaseEvents {
+    int phase;
+    cudaEvent_t a, b;
+};
+
+struct mertens_plan_s {
+    Allocator al;
+    std::vector<std::pair<void *, size_t>> allocs;
+    // targets
+    size_t nq = 0;
+    std::vector<uint64_t> n, u, X, off;
+    std::vector<uint64_t> direct, gathered, ymax_q;
+    uint64_t nent = 0;
+    uint64_t y_max = 0, block_len = 0, nblocks = 0, ydense = 0, jmax = 0, mg_n = 0;
+    uint64_t terms = 0;
+    // device buffers
+    PrimeTable pt;
+    uint64_t *dK = nullptr, *dJLO = nullptr, *dJC0 = nullptr, *dJCUR = nullptr, *dYCE = nullptr;
+    uint64_t *dJTOP = nullptr, *dJBOT = nullptr, *dS = nullptr, *dR = nullptr;
+    uint32_t *dICNT = nullptr, *dIOFF = nullptr, *dScan = nullptr;
+    int8_t *dmu_blk = nullptr, *dmu_aux = nullptr;
+    int32_t *dM_blk = nullptr, *dtile_sum = nullptr;
+    int64_t *dtile_off = nullptr, *dcarry = nullptr;
+    uint32_t *derr = nullptr, *dcounter = nullptr;
+    uint64_t *dMG = nullptr, *ddl_m = nullptr;
+    uint16_t *ddl_yo = nullptr;
+    uint32_t *ddl_cnt = nullptr;
+    Group *dgroups = nullptr;
+    DenseItem *ditems = nullptr;
+    uint32_t nitems = 0;
+    QueryDev *dqs = nullptr;
+    bool mg_built = false;
+    // run state
+    cudaEvent_t done = nullptr;
+    bool ran = false;
+    bool prof = false;
+    std::vector<PhaseEvents> evs;  // every timed phase since profiling was enabled
+    uint64_t prof_runs = 0;
+    uint64_t kernels = 0;
+    uint64_t h2d_bytes = 0, d2h_bytes = 0;
+
+    template <typename T>
+    T *alloc(size_t count)
+    {
+        size_t bytes = count * sizeof(T);
+        void *p = dev_alloc(al, bytes);
+        if (p)
+            allocs.push_back({p, bytes});
+        return (T *)p;
+    }
+};
+
+static double dense_factor()
+{
+    const char *e = getenv("MERTENS_DENSE_C");
+    double c = e ? atof(e) : 1.6;
+    return c > 0 ? c : 1.6;
+}
+
+// Shape of one target (host only): X, y_max and the closed-form term counts.
+static int describe_target(uint64_t n, uint64_t u, uint64_t *X, uint64_t *direct,
+                           uint64_t *gathered)
+{
+    *X = n / u;
+    uint64_t d = 0, g = 0;
+    for (uint64_t x = 1; x <= *X; ++x) {
+        const uint64_t k = n / x, s = isqrt64(k);
+        const uint64_t jlo = k / u + 1, jhi = k / (s + 1);
+        d += s;
+        if (jhi >= jlo)
+            g += jhi - jlo + 1;
+    }
+    *direct = d;
+    *gathered = g;
+    return 0;
+}
+
+static uint64_t auto_u(uint64_t n, size_t count)
+{
+    if (n <= 3)
+        return n;
+    double f = 0.9;
+    uint64_t u = (uint64_t)(f * std::pow((double)n * (double)count, 2.0 / 3.0));
+    const uint64_t r = isqrt64(n);
+    if (u <= r)
+        u = r + 1;
+    if (u > n)
+        u = n;
+    return u;
+}
+
+static int check_u(uint64_t n, uint64_t u)
+{
+    if (n == 1)
+        return u == 1 ? MERTENS_OK : MERTENS_EINVAL;
+    const uint64_t r = isqrt64(n);
+    if (u <= r || u > n)
+        return MERTENS_EINVAL;
+    return MERTENS_OK;
+}
+
+extern "C" {
+
+const char *mertens_strerror(int code)
+{
+    switch (code) {
+    case MERTENS_OK: return "ok";
+    case MERTENS_EINVAL: return "invalid argument";
+    case MERTENS_ENOMEM: return "out of memory";
+    case MERTENS_ECUDA: return "CUDA runtime error";
+    case MERTENS_ETIMEOUT: return "bounded device wait expired";
+    case MERTENS_ENOTREADY: return "no run to read";
+    case MERTENS_ENOTSUP: return "not supported by this build";
+    case MERTENS_EOVERFLOW: return "integer overflow in M(y) block";
+    default: return "unknown status";
+    }
+}
+
+const char *mertens_last_error(void) { return g_last_error; }
+
+int mertens_set_allocator(mertens_alloc_fn alloc, mertens_free_fn release, void *ctx)
+{
+    if (alloc && !release) {
+        set_last_error("mertens_set_allocator: alloc without release");
+        return MERTENS_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_alloc = alloc;
+    g_free = alloc ? release : nullptr;
+    g_alloc_ctx = alloc ? ctx : nullptr;
+    return MERTENS_OK;
+}
+
+int mertens_describe(mertens_u128 n, mertens_u128 u, mertens_query_info *info)
+{
+    if (!info || (n.lo == 0 && n.hi == 0)) {
+        set_last_error("mertens_describe: n must be >= 1");
+        return MERTENS_EINVAL;
+    }
+    if (n.hi != 0 || n.lo >= (1ull << 63) || u.hi != 0) {
+        set_last_error("mertens_describe: n >= 2^63 is not supported by this build");
+        return MERTENS_ENOTSUP;
+    }
+    uint64_t uu = u.lo ? u.lo : auto_u(n.lo, 1);
+    if (check_u(n.lo, uu) != MERTENS_OK) {
+        set_last_error("mertens_describe: u must satisfy floor(sqrt(n)) < u <= n");
+        return MERTENS_EINVAL;
+    }
+    memset(info, 0, sizeof(*info));
+    info->n = n;
+    info->u.lo = uu;
+    uint64_t X, d, g;
+    describe_target(n.lo, uu, &X, &d, &g);
+    info->X = X;
+    info->direct_terms = d;
+    info->gathered_terms = g;
+    // largest y read: the direct range ends at s <= sqrt(n); the gathered
+    // range of x = 1 ends at floor(n/(X+1)).
+    const uint64_t r = isqrt64(n.lo);
+    const uint64_t yg = n.lo / (X + 1);
+    info->y_max = std::max(r, yg);
+    return MERTENS_OK;
+}
+
+int mertens_plan(mertens_plan_t *out, const mertens_u128 *n, size_t count, mertens_u128 u,
+                 uint64_t block_len)
+{
+    if (!out)
+        return MERTENS_EINVAL;
+    *out = nullptr;
+    if (!n || count == 0 || count > (1u << 20)) {
+        set_last_error("mertens_plan: need 1 <= count <= 2^20 targets");
+        return MERTENS_EINVAL;
+    }
+    if (u.hi != 0) {
+        set_last_error("mertens_plan: u >= 2^64 is not supported by this build");
+        return MERTENS_ENOTSUP;
+    }
+    for (size_t i = 0; i < count; ++i) {
+        if (n[i].lo == 0 && n[i].hi == 0) {
+            set_last_error("mertens_plan: n[%zu] = 0", i);
+            return MERTENS_EINVAL;
+        }
+        if (n[i].hi != 0 || n[i].lo >= (1ull << 63)) {
+            set_last_error("mertens_plan: n[%zu] >= 2^63 needs the two-word path (not built)", i);
+            return MERTENS_ENOTSUP;
+        }
+        if (u.lo != 0 && check_u(n[i].lo, u.lo) != MERTENS_OK) {
+            set_last_error("mertens_plan: u = %llu invalid for n[%zu] = %llu "
+                           "(need floor(sqrt(n)) < u <= n)",
+                           (unsigned long long)u.lo, i, (unsigned long long)n[i].lo);
+            return MERTENS_EINVAL;
+        }
+    }
+    mertens_plan_s *p = new (std::nothrow) mertens_plan_s();
+    if (!p)
+        return MERTENS_ENOMEM;
+    p->al = current_allocator();
+    p->nq = count;
+    const double dc = dense_factor();
+
+    // ---- per-entry host planning ----
+    std::vector<uint64_t> K, JLO, JC0, YCE;
+    std::vector<Group> groups;
+    for (size_t i = 0; i < count; ++i) {
+        const uint64_t nn = n[i].lo;
+        const uint64_t uu = u.lo ? u.lo : auto_u(nn, count);
+        const uint64_t X = nn / uu;
+        p->n.push_back(nn);
+        p->u.push_back(uu);
+        p->X.push_back(X);
+        p->off.push_back(K.size());
+        uint64_t d = 0, g = 0, ymq = 0;
+        std::vector<uint64_t> S_(32), VH(32);
+        for (uint64_t x0 = 1; x0 <= X; x0 += 32) {
+            const uint32_t cnt = (uint32_t)std::min<uint64_t>(32, X - x0 + 1);
+            uint64_t lo = 0, hi = UINT64_MAX;
+            for (uint32_t t = 0; t < cnt; ++t) {
+                const uint64_t x = x0 + t, k = nn / x, s = isqrt64(k);
+                const uint64_t jlo = k / uu + 1, jhi = k / (s + 1);
+                // valid dense cut-offs: [s, floor(k/jlo) - 1] when the entry
+                // has gathered terms, else exactly s
+                const uint64_t vh = (jlo <= jhi) ? (k / jlo - 1) : s;
+                S_[t] = s;
+                VH[t] = vh;
+                lo = std::max(lo, s);
+                hi = std::min(hi, vh);
+                d += s;
+                if (jhi >= jlo)
+                    g += jhi - jlo + 1;
+                K.push_back(k);
+                JLO.push_back(jlo);
+            }
+            const uint64_t kf = nn / x0;
+            uint64_t target = (uint64_t)(dc * std::sqrt((double)kf));
+            target = ((target + 1 + kChunk - 1) / kChunk) * kChunk - 1;  // chunk aligned
+            Group G;
+            G.first = (uint32_t)(K.size() - cnt);
+            G.count = cnt;
+            G.pad = 0;
+            if (lo <= hi) {
+                const uint64_t yc = std::min(std::max(target, lo), hi);
+                G.pred = 0;
+                G.yc = yc;
+                for (uint32_t t = 0; t < cnt; ++t)
+                    YCE.push_back(yc);
+            } else {
+                G.pred = 1;
+                G.yc = 0;
+                for (uint32_t t = 0; t < cnt; ++t) {
+                    const uint64_t yc = std::min(std::max(target, S_[t]), VH[t]);
+                    YCE.push_back(yc);
+                    G.yc = std::max(G.yc, yc);
+                }
+            }
+            groups.push_back(G);
+            for (uint32_t t = 0; t < cnt; ++t) {
+                const size_t e = G.first + t;
+                const uint64_t k = K[e], yc = YCE[e];
+                const uint64_t jc0 = k / (yc + 1);
+                JC0.push_back(jc0);
+                uint64_t need = yc;
+                if (JLO[e] <= jc0)
+                    need = std::max(need, k / JLO[e]);
+                ymq = std::max(ymq, need);
+                p->ydense = std::max(p->ydense, yc);
+                p->jmax = std::max(p->jmax, jc0);
+            }
+        }
+        p->direct.push_back(d);
+        p->gathered.push_back(g);
+        p->ymax_q.push_back(ymq);
+        p->terms += d + g;
+        p->y_max = std::max(p->y_max, ymq);
+    }
+    p->nent = K.size();
+    if (p->nent >= (1ull << 32)) {
+        set_last_error("mertens_plan: more than 2^32 array entries");
+        delete p;
+        return MERTENS_ENOTSUP;
+    }
+    if (block_len == 0)
+        block_len = std::min<uint64_t>(((p->y_max + kSieveTile - 1) / kSieveTile) * kSieveTile,
+                                       1ull << 28);
+    if (block_len > (1ull << 31)) {
+        set_last_error("mertens_plan: block_len must be <= 2^31");
+        delete p;
+        return MERTENS_EINVAL;
+    }
+    p->block_len = block_len;
+    p->nblocks = (p->y_max + block_len - 1) / block_len;
+    p->mg_n = std::max(p->jmax, p->ydense) + 1;
+
+    // ---- dense work items: groups sorted by cut-off, chunk ranges ----
+    std::vector<uint32_t> order(groups.size());
+    for (size_t i = 0; i < order.size(); ++i)
+        order[i] = (uint32_t)i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](uint32_t a, uint32_t b) { return groups[a].yc > groups[b].yc; });
+    std::vector<Group> sg(groups.size());
+    for (size_t i = 0; i < order.size(); ++i)
+        sg[i] = groups[order[i]];
+    const uint64_t nchunks = p->ydense / kChunk + 1;
+    std::vector<DenseItem> items;
+    const uint32_t gpi = (kDenseThreads / 32) * 4;
+    size_t pref = sg.size();
+    for (uint64_t c0 = 0; c0 < nchunks; c0 += kDenseChunks) {
+        const uint64_t ys = c0 * kChunk;
+        while (pref > 0 && sg[pref - 1].yc < ys)
+            --pref;
+        if (pref == 0)
+            break;
+        for (size_t g0 = 0; g0 < pref; g0 += gpi) {
+            DenseItem it;
+            it.c0 = (uint32_t)c0;
+            it.c1 = (uint32_t)std::min<uint64_t>(c0 + kDenseChunks, nchunks);
+            it.g0 = (uint32_t)g0;
+            it.g1 = (uint32_t)std::min<size_t>(g0 + gpi, pref);
+            items.push_back(it);
+        }
+    }
+    p->nitems = (uint32_t)items.size();
+
+    // ---- device buffers ----
+    int rc = MERTENS_OK;
+    const size_t E = p->nent;
+    p->dK = p->alloc<uint64_t>(E);
+    p->dJLO = p->alloc<uint64_t>(E);
+    p->dJC0 = p->alloc<uint64_t>(E);
+    p->dJCUR = p->alloc<uint64_t>(E);
+    p->dYCE = p->alloc<uint64_t>(E);
+    p->dJTOP = p->alloc<uint64_t>(E);
+    p->dJBOT = p->alloc<uint64_t>(E);
+    p->dS = p->alloc<uint64_t>(E);
+    p->dR = p->alloc<uint64_t>(E);
+    p->dICNT = p->alloc<uint32_t>(E);
+    p->dIOFF = p->alloc<uint32_t>(E + 1);
+    p->dScan = p->alloc<uint32_t>(scan_scratch_words(E));
+    const uint64_t L = block_len;
+    const uint64_t tiles = sieve_tiles(L);
+    p->dmu_blk = p->alloc<int8_t>(((L + 15) / 16) * 16);
+    p->dmu_aux = p->alloc<int8_t>(p->ydense + 16);
+    p->dM_blk = p->alloc<int32_t>(L);
+    p->dtile_sum = p->alloc<int32_t>(tiles);
+    p->dtile_off = p->alloc<int64_t>(tiles);
+    p->dcarry = p->alloc<int64_t>(1);
+    p->derr = p->alloc<uint32_t>(1);
+    p->dcounter = p->alloc<uint32_t>(1);
+    p->dMG = p->alloc<uint64_t>(p->mg_n + 1);
+    p->ddl_m = p->alloc<uint64_t>(nchunks * kChunkCapPad);
+    p->ddl_yo = p->alloc<uint16_t>(nchunks * kChunkCapPad);
+    p->ddl_cnt = p->alloc<uint32_t>(nchunks);
+    p->dgroups = p->alloc<Group>(sg.size());
+    p->ditems = p->alloc<DenseItem>(items.size());
+    p->dqs = p->alloc<QueryDev>(count);
+    for (auto &a : p->allocs)
+        if (!a.first)
+            rc = MERTENS_ENOMEM;
+    bool any_null = !p->dK || !p->dJLO || !p->dJC0 || !p->dJCUR || !p->dYCE || !p->dJTOP ||
+                    !p->dJBOT || !p->dS || !p->dR || !p->dICNT || !p->dIOFF || !p->dScan ||
+                    !p->dmu_blk || !p->dmu_aux || !p->dM_blk || !p->dtile_sum ||
+                    !p->dtile_off || !p->dcarry || !p->derr || !p->dcounter || !p->dMG ||
+                    !p->ddl_m || !p->ddl_yo || !p->ddl_cnt || !p->dgroups || !p->ditems ||
+                    !p->dqs;
+    if (any_null)
+        rc = MERTENS_ENOMEM;
+    if (rc == MERTENS_OK) {
+        int prc = prime_table_create(&p->pt, p->al, p->y_max, nullptr);
+        if (prc != 0)
+            rc = prc == 6 ? MERTENS_ENOTSUP : (prc == 2 ? MERTENS_ENOMEM : MERTENS_ECUDA);
+    }
+    if (rc == MERTENS_OK) {
+        std::vector<QueryDev> qs(count);
+        for (size_t i = 0; i < count; ++i) {
+            qs[i].X = p->X[i];
+            qs[i].off = p->off[i];
+        }
+        cudaMemcpy(p->dK, K.data(), E * 8, cudaMemcpyHostToDevice);
+        cudaMemcpy(p->dJLO, JLO.data(), E * 8, cudaMemcpyHostToDevice);
+        cudaMemcpy(p->dJC0, JC0.data(), E * 8, cudaMemcpyHostToDevice);
+        cudaMemcpy(p->dYCE, YCE.data(), E * 8, cudaMemcpyHostToDevice);
+        cudaMemcpy(p->dgroups, sg.data(), sg.size() * sizeof(Group), cudaMemcpyHostToDevice);
+        if (!items.empty())
+            cudaMemcpy(p->ditems, items.data(), items.size() * sizeof(DenseItem),
+                       cudaMemcpyHostToDevice);
+        cudaMemcpy(p->dqs, qs.data(), count * sizeof(QueryDev), cudaMemcpyHostToDevice);
+        p->h2d_bytes = 4 * E * 8 + sg.size() * sizeof(Group) + items.size() * sizeof(DenseItem) +
+                       count * sizeof(QueryDev);
+        if (cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaGetLastError() != cudaSuccess)
+            rc = MERTENS_ECUDA;
+    }
+    if (rc != MERTENS_OK) {
+        if (rc == MERTENS_ENOMEM)
+            set_last_error("mertens_plan: device allocation failed");
+        else if (rc == MERTENS_ECUDA)
+            set_last_error("mertens_plan: CUDA error %s", cudaGetErrorString(cudaGetLastError()));
+        mertens_destroy(p);
+        return rc;
+    }
+    *out = p;
+    return MERTENS_OK;
+}
+
+static void ev_begin(mertens_plan_s *p, int phase, cudaStream_t s, PhaseEvents *pe)
+{
+    if (!p->prof)
+        return;
+    pe->phase = phase;
+    cudaEventCreate(&pe->a);
+    cudaEventCreate(&pe->b);
+    cudaEventRecord(pe->a, s);
+}
+
+static void ev_end(mertens_plan_s *p, cudaStream_t s, PhaseEvents *pe)
+{
+    if (!p->prof)
+        return;
+    cudaEventRecord(pe->b, s);
+    p->evs.push_back(*pe);
+}
+
+static void clear_events(mertens_plan_s *p)
+{
+    for (auto &e : p->evs) {
+        cudaEventDestroy(e.a);
+        cudaEventDestroy(e.b);
+    }
+    p->evs.clear();
+    p->prof_runs = 0;
+}
+
+int mertens_run(mertens_plan_t p, void *stream)
+{
+    if (!p) {
+        set_last_error("mertens_run: NULL plan");
+        return MERTENS_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    PhaseEvents total;
+    ev_begin(p, kPhTotal, s, &total);
+    uint64_t launches = 0;
+    int r;
+    const size_t E = p->nent;
+    cudaMemsetAsync(p->dS, 0, E * 8, s);
+    cudaMemcpyAsync(p->dJCUR, p->dJC0, E * 8, cudaMemcpyDeviceToDevice, s);
+    cudaMemsetAsync(p->dcarry, 0, 8, s);
+    cudaMemsetAsync(p->derr, 0, 4, s);
+    if (!p->mg_built) {
+        r = magic_table_enqueue(p->dMG, p->mg_n, s);
+        if (r < 0)
+            goto fail;
+        launches += r;
+        p->mg_built = true;
+    }
+    {
+        bool dense_done = false;
+        for (uint64_t b = 0; b < p->nblocks; ++b) {
+            const uint64_t y1 = 1 + b * p->block_len;
+            const uint64_t y2 = std::min(y1 + p->block_len - 1, p->y_max);
+            SieveLaunch L;
+            L.y1 = y1;
+            L.len = y2 - y1 + 1;
+            L.mu = p->dmu_blk;
+            L.mu_aux = (y1 <= p->ydense) ? p->dmu_aux : nullptr;
+            L.aux_end = p->ydense;
+            L.M = p->dM_blk;
+            L.tile_sum = p->dtile_sum;
+            L.tile_off = p->dtile_off;
+            L.carry = p->dcarry;
+            L.err = p->derr;
+            PhaseEvents pe, pe2;
+            ev_begin(p, kPhSieve, s, &pe);
+            if (p->prof) {
+                pe2.phase = kPhScan;
+                cudaEventCreate(&pe2.a);
+                cudaEventCreate(&pe2.b);
+                L.mid = pe.b;
+                L.mid2 = pe2.a;
+            }
+            r = sieve_block_enqueue(&p->pt, L, s);
+            if (p->prof) {
+                p->evs.push_back(pe);
+                cudaEventRecord(pe2.b, s);
+                p->evs.push_back(pe2);
+            }
+            if (r < 0)
+                goto fail;
+            launches += r;
+            if (!dense_done && y2 >= p->ydense) {
+                ev_begin(p, kPhDense, s, &pe);
+                r = dense_list_enqueue(p->dmu_aux, p->ydense, p->dMG, p->ddl_m, p->ddl_yo,
+                                       p->ddl_cnt, s);
+                if (r < 0)
+                    goto fail;
+                launches += r;
+                DenseArgs da;
+                da.items = p->ditems;
+                da.nitems = p->nitems;
+                da.counter = p->dcounter;
+                da.groups = p->dgroups;
+                da.K = p->dK;
+                da.YCE = p->dYCE;
+                da.dl_m = p->ddl_m;
+                da.dl_yo = p->ddl_yo;
+                da.dl_cnt = p->ddl_cnt;
+                da.S = p->dS;
+                r = dense_update_enqueue(da, s);
+                ev_end(p, s, &pe);
+                if (r < 0)
+                    goto fail;
+                launches += r;
+                dense_done = true;
+            }
+            SparseBlockArgs sb;
+            sb.y1 = y1;
+            sb.y2 = y2;
+            sb.m_y1 = magic_of(y1);
+            sb.l_y1 = magic_shift(y1);
+            sb.m_y2p1 = magic_of(y2 + 1);
+            sb.l_y2p1 = magic_shift(y2 + 1);
+            SparseArgs sa;
+            sa.nent = E;
+            sa.K = p->dK;
+            sa.JLO = p->dJLO;
+            sa.JC0 = p->dJC0;
+            sa.YCE = p->dYCE;
+            sa.MG = p->dMG;
+            sa.JCUR = p->dJCUR;
+            sa.JTOP = p->dJTOP;
+            sa.JBOT = p->dJBOT;
+            sa.S = p->dS;
+            sa.ICNT = p->dICNT;
+            sa.IOFF = p->dIOFF;
+            sa.Mblk = p->dM_blk;
+            ev_begin(p, kPhGather, s, &pe);
+            r = sparse_block_enqueue(sb, sa, p->dScan, s);
+            ev_end(p, s, &pe);
+            if (r < 0)
+                goto fail;
+            launches += r;
+        }
+        PhaseEvents pe;
+        ev_begin(p, kPhResolve, s, &pe);
+        r = resolve_enqueue(p->dqs, (uint32_t)p->nq, p->dS, p->dK, p->dR, s);
+        ev_end(p, s, &pe);
+        if (r < 0)
+            goto fail;
+        launches += r;
+    }
+    ev_end(p, s, &total);
+    if (p->prof)
+        ++p->prof_runs;
+    if (cudaEventRecord(p->done, s) != cudaSuccess)
+        goto fail;
+    p->kernels = launches;
+    p->d2h_bytes = 0;
+    p->ran = true;
+    return MERTENS_OK;
+fail:
+    set_last_error("mertens_run: launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return MERTENS_ECUDA;
+}
+
+int mertens_result(mertens_plan_t p, size_t i, int64_t *M_n, int64_t *entries, size_t cap,
+                   size_t *len)
+{
+    if (!p || i >= p->nq) {
+        set_last_error("mertens_result: bad plan or index");
+        return MERTENS_EINVAL;
+    }
+    if (!p->ran) {
+        set_last_error("mertens_result: mertens_run was not called");
+        return MERTENS_ENOTREADY;
+    }
+    if (cudaEventSynchronize(p->done) != cudaSuccess) {
+        set_last_error("mertens_result: %s", cudaGetErrorString(cudaGetLastError()));
+        return MERTENS_ECUDA;
+    }
+    uint32_t err = 0;
+    if (cudaMemcpy(&err, p->derr, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return MERTENS_ECUDA;
+    if (err & kErrMOverflow) {
+        set_last_error("mertens_result: |M(y)| exceeded the int32 block type");
+        return MERTENS_EOVERFLOW;
+    }
+    if (len)
+        *len = p->X[i];
+    const uint64_t o = p->off[i];
+    if (M_n) {
+        if (cudaMemcpy(M_n, p->dR + o, 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return MERTENS_ECUDA;
+        p->d2h_bytes += 8;
+    }
+    if (entries && cap) {
+        const size_t m = std::min<size_t>(cap, p->X[i]);
+        if (cudaMemcpy(entries, p->dR + o, m * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return MERTENS_ECUDA;
+        p->d2h_bytes += m * 8;
+    }
+    return MERTENS_OK;
+}
+
+void mertens_destroy(mertens_plan_t p)
+{
+    if (!p)
+        return;
+    if (p->done) {
+        cudaEventSynchronize(p->done);
+        cudaEventDestroy(p->done);
+    }
+    clear_events(p);
+    if (p->pt.np)
+        prime_table_destroy(&p->pt);
+    for (auto &a : p->allocs)
+        dev_free(p->al, a.first, a.second);
+    delete p;
+}
+
+int mertens_plan_info(mertens_plan_t p, size_t i, mertens_query_info *info)
+{
+    if (!p || i >= p->nq || !info)
+        return MERTENS_EINVAL;
+    memset(info, 0, sizeof(*info));
+    info->n.lo = p->n[i];
+    info->u.lo = p->u[i];
+    info->X = p->X[i];
+    info->y_max = p->ymax_q[i];
+    info->direct_terms = p->direct[i];
+    info->gathered_terms = p->gathered[i];
+    return MERTENS_OK;
+}
+
+int mertens_plan_set_profiling(mertens_plan_t p, int enable)
+{
+    if (!p)
+        return MERTENS_EINVAL;
+    if (p->done)
+        cudaEventSynchronize(p->done);
+    clear_events(p);
+    p->prof = enable != 0;
+    return MERTENS_OK;
+}
+
+int mertens_run_stats_get(mertens_plan_t p, mertens_run_stats *st)
+{
+    if (!p || !st)
+        return MERTENS_EINVAL;
+    memset(st, 0, sizeof(*st));
+    if (!p->ran)
+        return MERTENS_ENOTREADY;
+    if (cudaEventSynchronize(p->done) != cudaSuccess)
+        return MERTENS_ECUDA;
+    st->blocks = p->nblocks;
+    st->y_sieved = p->y_max;
+    st->terms = p->terms;
+    st->kernels = p->kernels;
+    st->h2d_bytes = p->h2d_bytes;
+    st->d2h_bytes = p->d2h_bytes;
+    st->runs = p->prof_runs;
+    if (p->prof_runs) {
+        double acc[kPhases] = {0, 0, 0, 0, 0, 0};
+        for (auto &e : p->evs) {
+            float t = 0;
+            cudaEventElapsedTime(&t, e.a, e.b);
+            acc[e.phase] += t;
+        }
+        const double r = (double)p->prof_runs;
+        st->sieve_ms = acc[kPhSieve] / r;
+        st->scan_ms = acc[kPhScan] / r;
+        st->dense_ms = acc[kPhDense] / r;
+        st->gather_ms = acc[kPhGather] / r;
+        st->update_ms = (acc[kPhDense] + acc[kPhGather]) / r;
+        st->resolve_ms = acc[kPhResolve] / r;
+        st->total_ms = acc[kPhTotal] / r;
+    }
+    return MERTENS_OK;
+}
+
+// ---- step-level entry points ----
+static int sieve_window(uint64_t y1, uint64_t len, int8_t *mu_dev, int64_t carry, int32_t *M_dev,
+                        void *stream)
+{
+    if (y1 == 0 || len == 0 || len > (1ull << 31) || y1 + len - 1 < y1 ||
+        y1 + len - 1 >= (1ull << 62)) {
+        set_last_error("sieve: need y1 >= 1, 1 <= len <= 2^31, y1+len-1 < 2^62");
+        return MERTENS_EINVAL;
+    }
+    if (mu_dev && ((uintptr_t)mu_dev & 15u)) {
+        set_last_error("sieve: mu_dev must be 16-byte aligned");
+        return MERTENS_EINVAL;
+    }
+    if (M_dev && ((uintptr_t)M_dev & 3u)) {
+        set_last_error("sieve: M_dev must be 4-byte aligned");
+        return MERTENS_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    Allocator al = current_allocator();
+    PrimeTable pt;
+    int prc = prime_table_create(&pt, al, y1 + len - 1, s);
+    if (prc != 0) {
+        if (pt.np)
+            prime_table_destroy(&pt);
+        return prc == 6 ? MERTENS_ENOTSUP : (prc == 2 ? MERTENS_ENOMEM : MERTENS_ECUDA);
+    }
+    const uint64_t tiles = sieve_tiles(len);
+    int8_t *mu = mu_dev;
+    bool own_mu = false;
+    if (!mu) {
+        mu = (int8_t *)dev_alloc(al, ((len + 15) / 16) * 16);
+        own_mu = true;
+    }
+    int32_t *ts = (int32_t *)dev_alloc(al, tiles * 4);
+    int64_t *to = (int64_t *)dev_alloc(al, tiles * 8);
+    int64_t *cy = (int64_t *)dev_alloc(al, 8);
+    uint32_t *er = (uint32_t *)dev_alloc(al, 4);
+    int rc = MERTENS_OK;
+    if (!mu || !ts || !to || !cy || !er)
+        rc = MERTENS_ENOMEM;
+    if (rc == MERTENS_OK) {
+        cudaMemcpyAsync(cy, &carry, 8, cudaMemcpyHostToDevice, s);
+        cudaMemsetAsync(er, 0, 4, s);
+        SieveLaunch L;
+        L.y1 = y1;
+        L.len = len;
+        L.mu = mu;
+        L.M = M_dev;
+        L.tile_sum = ts;
+        L.tile_off = to;
+        L.carry = cy;
+        L.err = er;
+        if (sieve_block_enqueue(&pt, L, s) < 0)
+            rc = MERTENS_ECUDA;
+        uint32_t e = 0;
+        if (cudaMemcpyAsync(&e, er, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            rc = MERTENS_ECUDA;
+        if (rc == MERTENS_OK && (e & kErrMOverflow))
+            rc = MERTENS_EOVERFLOW;
+    }
+    if (rc == MERTENS_ECUDA)
+        set_last_error("sieve: %s", cudaGetErrorString(cudaGetLastError()));
+    if (own_mu)
+        dev_free(al, mu, ((len + 15) / 16) * 16);
+    dev_free(al, ts, tiles * 4);
+    dev_free(al, to, tiles * 8);
+    dev_free(al, cy, 8);
+    dev_free(al, er, 4);
+    prime_table_destroy(&pt);
+    return rc;
+}
+
+int mertens_sieve_mu(uint64_t y1, uint64_t len, int8_t *mu_dev, void *stream)
+{
+    if (!mu_dev)
+        return MERTENS_EINVAL;
+    return sieve_window(y1, len, mu_dev, 0, nullptr, stream);
+}
+
+int mertens_sieve_M(uint64_t y1, uint64_t len, int64_t carry, int32_t *M_dev, void *stream)
+{
+    if (!M_dev)
+        return MERTENS_EINVAL;
+    return sieve_window(y1, len, nullptr, carry, M_dev, stream);
+}
+
+}  // extern "C"

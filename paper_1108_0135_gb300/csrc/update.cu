@@ -1,0 +1,388 @@
+// Step a3 (mertens_update) and step a4 (resolve) of the isolated-value
+// Mertens method (arXiv:1108.0135, Sec. 2-3).
+//
+// Entry x of a target n has k = floor(n/x) and s = floor(sqrt(k)).  By the
+// split formula of Sec. 2 (taken at t = s+1) its array value is
+//   M(k) = 1 - sum_{j=2}^{floor(k/(s+1))} M(floor(k/j))
+//            - sum_{y=1}^{s} M(y) (floor(k/y) - floor(k/(y+1))).
+// The terms with j <= floor(k/u) are other array entries (added in resolve);
+// the rest -- direct terms y <= s and gathered terms j in
+// [floor(k/u)+1, floor(k/(s+1))] -- are accumulated into S[x] by the update.
+//
+// The update covers y in [1, yc] for a cut-off yc >= s (a "dense" range, the
+// paper's regions 1 and 1', Sec. 3) with the coefficient form
+//   sum_{y<=yc} M(y)(q(y) - q(y+1)) = sum_{y<=yc} mu(y) q(y) - M(yc) q(yc+1),
+// q(y) = floor(k/y) (summation by parts), which needs mu(y) and one quotient
+// per squarefree y; and it covers y > yc with the gathered form, one term
+// M(floor(k/j)) for each j in [floor(k/u)+1, floor(k/(yc+1))] (regions 2-4).
+// Both forms count every j >= floor(k/u)+1 exactly once, so the sum is the
+// same for any yc in [s, floor(k/(floor(k/u)+1)) - 1].
+#include <cstdint>
+
+#include "common.cuh"
+#include "internal.h"
+#include "update.h"
+
+namespace mert {
+
+// ---------------------------------------------------------------------------
+// Tables.
+// ---------------------------------------------------------------------------
+// MG[d] = division magic of d, d = 1..nd (MG[0] unused).
+__global__ void magic_table_kernel(uint64_t *__restrict__ MG, uint64_t nd)
+{
+    for (uint64_t d = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x + 1; d <= nd;
+         d += (uint64_t)gridDim.x * blockDim.x)
+        MG[d] = magic_of(d);
+}
+
+// Squarefree list of one chunk of kChunk y values (y <= ydense): the magics
+// of the y with mu = +1, then (from an even index) those with mu = -1, with
+// the offsets y - chunk start, in increasing y.  256 threads x 16 y.
+__global__ void __launch_bounds__(256) dense_list_kernel(const int8_t *__restrict__ mu_aux,
+                                                         uint64_t ydense,
+                                                         const uint64_t *__restrict__ MG,
+                                                         uint64_t *__restrict__ dl_m,
+                                                         uint16_t *__restrict__ dl_yo,
+                                                         uint32_t *__restrict__ dl_cnt)
+{
+    __shared__ uint32_t sh[33];
+    const uint64_t c = blockIdx.x;
+    const uint64_t cb = c * kChunk;
+    int8_t mv[16];
+    uint32_t cp = 0, cm = 0;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const uint64_t y = cb + threadIdx.x * 16 + k;
+        mv[k] = (y >= 1 && y <= ydense) ? mu_aux[y - 1] : (int8_t)0;
+        cp += mv[k] > 0;
+        cm += mv[k] < 0;
+    }
+    uint32_t totp, totm;
+    uint32_t ip = block_scan_u32(cp, sh, &totp);
+    uint32_t im = block_scan_u32(cm, sh, &totm);
+    const uint32_t np_pad = (totp + 1u) & ~1u;
+    uint64_t *dm = dl_m + c * kChunkCapPad;
+    uint16_t *dy = dl_yo + c * kChunkCapPad;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const uint32_t o = threadIdx.x * 16 + k;
+        const uint64_t y = cb + o;
+        if (mv[k] > 0) {
+            dm[ip] = MG[y];
+            dy[ip] = (uint16_t)o;
+            ++ip;
+        } else if (mv[k] < 0) {
+            dm[np_pad + im] = MG[y];
+            dy[np_pad + im] = (uint16_t)o;
+            ++im;
+        }
+    }
+    if (threadIdx.x == 0)
+        dl_cnt[c] = totp | (totm << 16);
+}
+
+// ---------------------------------------------------------------------------
+// Dense update: lanes = 32 array entries of one group, all reading the same
+// squarefree y (shared-memory broadcast); S[x] += sum mu(y) floor(k/y).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t upper_bound_u16(const uint16_t *a, uint32_t n, uint32_t v)
+{
+    uint32_t lo = 0, hi = n;  // first index with a[i] > v
+    while (lo < hi) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (a[mid] <= v)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// Sum of floor(k/y) over a staged list with the chunk's uniform shift l.
+__device__ __forceinline__ uint64_t quot_sum_uniform(uint64_t k2, const uint64_t *mp, uint32_t n,
+                                                     unsigned l)
+{
+    uint64_t a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    uint32_t i = 0;
+    const ulonglong2 *m2 = reinterpret_cast<const ulonglong2 *>(mp);
+    for (; i + 4 <= n; i += 4) {
+        const ulonglong2 u = m2[i >> 1];
+        const ulonglong2 v = m2[(i >> 1) + 1];
+        a0 += div_magic(k2, u.x, l);
+        a1 += div_magic(k2, u.y, l);
+        a2 += div_magic(k2, v.x, l);
+        a3 += div_magic(k2, v.y, l);
+    }
+    for (; i < n; ++i)
+        a0 += div_magic(k2, mp[i], l);
+    return (a0 + a1) + (a2 + a3);
+}
+
+// Same with a per-term shift (chunk 0) and/or a per-lane cut-off y <= ycl.
+__device__ __forceinline__ uint64_t quot_sum_general(uint64_t k2, const uint64_t *mp,
+                                                     const uint16_t *yp, uint32_t n, uint64_t cb,
+                                                     unsigned l, bool var_shift, uint64_t ycl)
+{
+    uint64_t a = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        const uint64_t y = cb + yp[i];
+        const unsigned li = var_shift ? magic_shift(y) : l;
+        const uint64_t q = div_magic(k2, mp[i], li);
+        a += (y <= ycl) ? q : 0ull;
+    }
+    return a;
+}
+
+__global__ void __launch_bounds__(kDenseThreads) dense_update_kernel(DenseArgs a)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    uint64_t *s_m = reinterpret_cast<uint64_t *>(smem);
+    uint16_t *s_yo = reinterpret_cast<uint16_t *>(s_m + kDenseChunks * kChunkCapPad);
+    __shared__ uint32_t s_item;
+    __shared__ uint32_t s_cnt[kDenseChunks];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (;;) {
+        if (threadIdx.x == 0)
+            s_item = atomicAdd(a.counter, 1u);
+        __syncthreads();
+        const uint32_t it = s_item;
+        if (it >= a.nitems)
+            break;
+        const DenseItem d = a.items[it];
+        for (uint32_t c = d.c0; c < d.c1; ++c) {
+            const uint32_t cnt = a.dl_cnt[c];
+            const uint32_t tot = (((cnt & 0xffffu) + 1u) & ~1u) + (cnt >> 16);
+            const uint64_t *src = a.dl_m + (uint64_t)c * kChunkCapPad;
+            const uint16_t *ysrc = a.dl_yo + (uint64_t)c * kChunkCapPad;
+            uint64_t *dst = s_m + (c - d.c0) * kChunkCapPad;
+            uint16_t *ydst = s_yo + (c - d.c0) * kChunkCapPad;
+            for (uint32_t i = threadIdx.x; i < tot; i += blockDim.x) {
+                dst[i] = src[i];
+                ydst[i] = ysrc[i];
+            }
+            if (threadIdx.x == 0)
+                s_cnt[c - d.c0] = cnt;
+        }
+        __syncthreads();
+        for (uint32_t g = d.g0 + warp; g < d.g1; g += nwarp) {
+            const Group G = a.groups[g];
+            const bool act = (uint32_t)lane < G.count;
+            const uint64_t e = (uint64_t)G.first + lane;
+            const uint64_t k2 = act ? (a.K[e] << 1) : 0ull;
+            const uint64_t ycl = G.pred ? (act ? a.YCE[e] : 0ull) : G.yc;
+            uint64_t accp = 0, accm = 0;
+            for (uint32_t c = d.c0; c < d.c1; ++c) {
+                const uint64_t cb = (uint64_t)c * kChunk;
+                if (cb > G.yc)
+                    break;
+                const uint32_t cnt = s_cnt[c - d.c0];
+                uint32_t np = cnt & 0xffffu, nm = cnt >> 16;
+                const uint32_t npad = (np + 1u) & ~1u;
+                const uint64_t *mp = s_m + (c - d.c0) * kChunkCapPad;
+                const uint16_t *yp = s_yo + (c - d.c0) * kChunkCapPad;
+                if (cb + kChunk - 1 > G.yc) {
+                    const uint32_t lim = (uint32_t)(G.yc - cb);
+                    np = upper_bound_u16(yp, np, lim);
+                    nm = upper_bound_u16(yp + npad, nm, lim);
+                }
+                const unsigned l = magic_shift((c + 1) * (uint64_t)kChunk - 1);
+                if (c == 0 || G.pred) {
+                    accp += quot_sum_general(k2, mp, yp, np, cb, l, c == 0, ycl);
+                    accm += quot_sum_general(k2, mp + npad, yp + npad, nm, cb, l, c == 0, ycl);
+                } else {
+                    accp += quot_sum_uniform(k2, mp, np, l);
+                    accm += quot_sum_uniform(k2, mp + npad, nm, l);
+                }
+            }
+            if (act)
+                atomicAdd(reinterpret_cast<unsigned long long *>(a.S + e),
+                          (unsigned long long)(accp - accm));
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Gathered terms of one sieve block [y1, y2].
+// ---------------------------------------------------------------------------
+// Per entry: the j-range of the block, j in [max(jlo, floor(k/(y2+1))+1),
+// min(jcur, floor(k/y1))] (so floor(k/j) lies in the block), its number of
+// warp items, and the cursor for the next block.  Also adds the boundary
+// term -M(yc) floor(k/(yc+1)) of the dense form when yc is in this block.
+__global__ void sparse_prep_kernel(SparseBlockArgs b, SparseArgs a)
+{
+    const uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= a.nent)
+        return;
+    const uint64_t k2 = a.K[e] << 1;
+    const uint64_t jc = a.JCUR[e], jlo = a.JLO[e];
+    const uint64_t q1 = div_magic(k2, b.m_y1, b.l_y1);      // floor(k / y1)
+    const uint64_t q2 = div_magic(k2, b.m_y2p1, b.l_y2p1);  // floor(k / (y2+1))
+    const uint64_t jtop = jc < q1 ? jc : q1;
+    const uint64_t jbot = (q2 + 1) > jlo ? (q2 + 1) : jlo;
+    const uint64_t cnt = jtop >= jbot ? jtop - jbot + 1 : 0;
+    a.JTOP[e] = jtop;
+    a.JBOT[e] = jbot;
+    a.ICNT[e] = (uint32_t)((cnt + kSparseItem - 1) / kSparseItem);
+    a.JCUR[e] = jc < q2 ? jc : q2;
+    const uint64_t yc = a.YCE[e];
+    if (yc >= b.y1 && yc <= b.y2) {
+        const int64_t Myc = a.Mblk[yc - b.y1];
+        atomicAdd(reinterpret_cast<unsigned long long *>(a.S + e),
+                  (unsigned long long)(-(int64_t)((uint64_t)Myc * a.JC0[e])));
+    }
+}
+
+// One warp per item of kSparseItem consecutive j of one entry, lanes over j:
+// S[x] += sum M(floor(k/j)), M read from the block's M(y) array.
+__global__ void __launch_bounds__(256) sparse_update_kernel(SparseBlockArgs b, SparseArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t total = a.IOFF[a.nent];
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total; w += nw) {
+        uint64_t lo = 0, hi = a.nent;  // largest e with IOFF[e] <= w
+        while (hi - lo > 1) {
+            const uint64_t mid = (lo + hi) >> 1;
+            if (a.IOFF[mid] <= w)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        const uint64_t e = lo;
+        const uint64_t r = w - a.IOFF[e];
+        const uint64_t jt = a.JTOP[e] - r * kSparseItem;
+        const uint64_t jb0 = a.JBOT[e];
+        const uint64_t jb = (jt - jb0 + 1 > (uint64_t)kSparseItem) ? jt - kSparseItem + 1 : jb0;
+        const uint64_t k2 = a.K[e] << 1;
+        int64_t acc = 0;
+        for (uint64_t j = jt - lane; j >= jb && j <= jt; j -= 32) {
+            const uint64_t y = div_magic(k2, a.MG[j], magic_shift(j));
+            acc += a.Mblk[y - b.y1];
+        }
+        acc = warp_sum_i64(acc);
+        if (lane == 0)
+            atomicAdd(reinterpret_cast<unsigned long long *>(a.S + e), (unsigned long long)acc);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Resolve (Sec. 2): for x = X down to 1,
+//   M[x] = 1 - S[x] - sum_{j=2}^{floor(X/x)} M[x j]   (mod 2^64),
+// level by level: all x with the same q = floor(X/x) only read entries of
+// smaller q.  One CTA per target.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) resolve_kernel(const QueryDev *__restrict__ qs,
+                                                       const uint64_t *__restrict__ S,
+                                                       const uint64_t *__restrict__ K,
+                                                       uint64_t *__restrict__ R)
+{
+    const QueryDev Q = qs[blockIdx.x];
+    const uint64_t X = Q.X, base = Q.off;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    uint64_t xhi = X;
+    while (xhi >= 1) {
+        const uint64_t qv = X / xhi;
+        const uint64_t xlo = X / (qv + 1) + 1;
+        const uint64_t size = xhi - xlo + 1;
+        if (size >= blockDim.x || qv <= 8) {
+            for (uint64_t x = xlo + threadIdx.x; x <= xhi; x += blockDim.x) {
+                uint64_t acc = 0;
+                for (uint64_t j = 2; j <= qv; ++j)
+                    acc += R[base + x * j - 1];
+                const uint64_t e = base + x - 1;
+                R[e] = (K[e] == 1) ? 1ull : 1ull - S[e] - acc;
+            }
+        } else {
+            for (uint64_t x = xlo + warp; x <= xhi; x += nwarp) {
+                uint64_t acc = 0;
+                for (uint64_t j = 2 + lane; j <= qv; j += 32)
+                    acc += R[base + x * j - 1];
+                acc = warp_sum_u64(acc);
+                if (lane == 0) {
+                    const uint64_t e = base + x - 1;
+                    R[e] = (K[e] == 1) ? 1ull : 1ull - S[e] - acc;
+                }
+            }
+        }
+        __syncthreads();
+        xhi = xlo - 1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers.
+// ---------------------------------------------------------------------------
+int magic_table_enqueue(uint64_t *MG, uint64_t nd, cudaStream_t s)
+{
+    if (nd == 0)
+        return 0;
+    uint64_t blocks = (nd + 255) / 256;
+    if (blocks > 152 * 64)
+        blocks = 152 * 64;
+    magic_table_kernel<<<(unsigned)blocks, 256, 0, s>>>(MG, nd);
+    return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
+int dense_list_enqueue(const int8_t *mu_aux, uint64_t ydense, const uint64_t *MG, uint64_t *dl_m,
+                       uint16_t *dl_yo, uint32_t *dl_cnt, cudaStream_t s)
+{
+    const uint64_t nchunks = ydense / kChunk + 1;
+    dense_list_kernel<<<(unsigned)nchunks, 256, 0, s>>>(mu_aux, ydense, MG, dl_m, dl_yo, dl_cnt);
+    return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
+int dense_update_enqueue(const DenseArgs &a, cudaStream_t s)
+{
+    static bool attr = false;
+    const size_t smem = (size_t)kDenseChunks * kChunkCapPad * (8 + 2);
+    if (!attr) {
+        cudaFuncSetAttribute(dense_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        attr = true;
+    }
+    if (a.nitems == 0)
+        return 0;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, dense_update_kernel, kDenseThreads, smem);
+    if (per < 1)
+        per = 1;
+    uint32_t grid = (uint32_t)(sms * per);
+    if (grid > a.nitems)
+        grid = a.nitems;
+    cudaMemsetAsync(a.counter, 0, 4, s);
+    dense_update_kernel<<<grid, kDenseThreads, smem, s>>>(a);
+    return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
+int sparse_block_enqueue(const SparseBlockArgs &b, const SparseArgs &a, uint32_t *scan_scratch,
+                         cudaStream_t s)
+{
+    int launches = 0;
+    const unsigned pb = (unsigned)((a.nent + 255) / 256);
+    sparse_prep_kernel<<<pb, 256, 0, s>>>(b, a);
+    ++launches;
+    int r = exclusive_scan_u32(a.ICNT, a.IOFF, a.nent, scan_scratch, s);
+    if (r < 0)
+        return -1;
+    launches += r;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    sparse_update_kernel<<<sms * 8, 256, 0, s>>>(b, a);
+    ++launches;
+    return cudaGetLastError() == cudaSuccess ? launches : -1;
+}
+
+int resolve_enqueue(const QueryDev *qs, uint32_t nq, const uint64_t *S, const uint64_t *K,
+                    uint64_t *R, cudaStream_t s)
+{
+    resolve_kernel<<<nq, 1024, 0, s>>>(qs, S, K, R);
+    return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
+}  // namespace mert

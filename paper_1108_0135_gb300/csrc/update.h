@@ -1,0 +1,74 @@
+// Argument blocks of the update (a3) and resolve (a4) kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mert {
+
+// Chunks staged per dense work item, threads per dense CTA, and the padded
+// per-chunk capacity of the squarefree list (the mu = -1 part starts at an
+// even index so that both parts can be read 16 bytes at a time).
+constexpr int kDenseChunks = 2;
+constexpr int kDenseThreads = 256;
+constexpr int kChunkCapPad = 3074;
+
+// 32 consecutive entries of one target sharing one dense cut-off yc (pred =
+// 0), or with a cut-off per entry in YCE (pred = 1; yc = their maximum).
+struct Group {
+    uint32_t first;  // global index of the first entry
+    uint32_t count;  // entries in the group (1..32)
+    uint32_t pred;
+    uint32_t pad;
+    uint64_t yc;
+};
+
+// Dense work item: chunks [c0, c1) for the groups [g0, g1) of the sorted
+// group list.
+struct DenseItem {
+    uint32_t c0, c1, g0, g1;
+};
+
+struct DenseArgs {
+    const DenseItem *items;
+    uint32_t nitems;
+    uint32_t *counter;
+    const Group *groups;
+    const uint64_t *K;    // k = floor(n/x) per entry
+    const uint64_t *YCE;  // dense cut-off per entry
+    const uint64_t *dl_m;
+    const uint16_t *dl_yo;
+    const uint32_t *dl_cnt;
+    uint64_t *S;
+};
+
+// Invariant-divisor constants of one block [y1, y2].
+struct SparseBlockArgs {
+    uint64_t y1, y2;
+    uint64_t m_y1, m_y2p1;
+    uint32_t l_y1, l_y2p1;
+};
+
+struct SparseArgs {
+    uint64_t nent;
+    const uint64_t *K, *JLO, *JC0, *YCE, *MG;
+    uint64_t *JCUR, *JTOP, *JBOT, *S;
+    uint32_t *ICNT, *IOFF;
+    const int32_t *Mblk;
+};
+
+struct QueryDev {
+    uint64_t X;    // entries of the target
+    uint64_t off;  // global index of its entry x = 1
+};
+
+int magic_table_enqueue(uint64_t *MG, uint64_t nd, cudaStream_t s);
+int dense_list_enqueue(const int8_t *mu_aux, uint64_t ydense, const uint64_t *MG, uint64_t *dl_m,
+                       uint16_t *dl_yo, uint32_t *dl_cnt, cudaStream_t s);
+int dense_update_enqueue(const DenseArgs &a, cudaStream_t s);
+int sparse_block_enqueue(const SparseBlockArgs &b, const SparseArgs &a, uint32_t *scan_scratch,
+                         cudaStream_t s);
+int resolve_enqueue(const QueryDev *qs, uint32_t nq, const uint64_t *S, const uint64_t *K,
+                    uint64_t *R, cudaStream_t s);
+
+}  // namespace mert

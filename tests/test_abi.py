@@ -1,0 +1,77 @@
+"""The C-ABI library without a GPU: it builds, loads, exports every symbol
+include/libmertens.h declares, and its host-only planning calls agree with
+the oracle's enumeration."""
+import ctypes
+import math
+import os
+import re
+
+import pytest
+
+import oracle
+import paper_1108_0135_gb300 as pm
+from tests.conftest import ROOT
+
+
+def header_functions():
+    text = open(os.path.join(ROOT, "include", "libmertens.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(mertens_[A-Za-z_0-9]+)\s*\(",
+                           text, flags=re.M))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = pm.load()
+    declared = header_functions()
+    assert len(declared) >= 13
+    assert set(declared) == set(pm.EXPORTS)
+    for name in declared:
+        assert hasattr(lib, name), name
+        assert isinstance(getattr(lib, name), ctypes._CFuncPtr)
+
+
+def test_strerror_covers_codes():
+    for code in range(8):
+        assert pm.mertens_strerror(code) != "unknown status"
+    assert pm.mertens_strerror(99) == "unknown status"
+
+
+@pytest.mark.parametrize("n", [2, 3, 10, 97, 100, 399])
+def test_describe_term_counts_match_enumeration(n):
+    s = math.isqrt(n)
+    for u in range(s + 1, n + 1):
+        info = pm.mertens_describe(n, u)
+        assert info["X"] == n // u
+        assert (info["direct_terms"], info["gathered_terms"]) == oracle.count_terms(n, u)
+
+
+def test_describe_full_size_counts():
+    info = pm.mertens_describe(10**16, 4 * 10**10)
+    assert info["X"] == 250_000
+    total = info["direct_terms"] + info["gathered_terms"]
+    assert 1.99e11 < total < 2.0e11
+    info = pm.mertens_describe(10**12, 10**8)
+    assert info["X"] == 10_000 and info["y_max"] == 10**12 // 10_001
+
+
+@pytest.mark.parametrize("n,u,code", [
+    (0, 0, pm.MERTENS_EINVAL),
+    (100, 10, pm.MERTENS_EINVAL),       # u must exceed floor(sqrt(n))
+    (100, 101, pm.MERTENS_EINVAL),      # u must not exceed n
+    (2**63, 0, pm.MERTENS_ENOTSUP),     # two-word path not in this build
+])
+def test_invalid_arguments_rejected_without_gpu(n, u, code):
+    with pytest.raises(pm.MertensError) as ei:
+        pm.mertens_describe(n, u)
+    assert ei.value.code == code
+    with pytest.raises(pm.MertensError) as ei:
+        pm.mertens_plan([n], u)
+    assert ei.value.code == code
+
+
+def test_plan_rejects_empty_batch():
+    lib = pm.load()
+    h = ctypes.c_void_p()
+    rc = lib.mertens_plan(ctypes.byref(h), None, 0, pm._lib.u128(0), 0)
+    assert rc == pm.MERTENS_EINVAL and not h.value

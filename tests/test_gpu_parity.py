@@ -1,0 +1,215 @@
+"""CUDA path against the CPU oracle, element by element, bit-exact.
+
+Every call goes through the C ABI (libmertens.so via its ctypes binding).
+Small cases compare whole arrays; the full-size n = 10^16 configuration is
+checked against Table 1 of the paper and on sampled entries the oracle
+computes one by one.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1108_0135_gb300 as pm
+from paper_1108_0135_gb300 import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TILE = 32768
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pm.load()
+    yield
+
+
+def gpu_array(n, u=0, block_len=0):
+    plan = pm.mertens_plan([n], u, block_len)
+    try:
+        pm.mertens_run(plan)
+        m, arr = pm.mertens_result(plan, 0, entries=True)
+    finally:
+        pm.mertens_destroy(plan)
+    return m, arr
+
+
+# ---- a1, a2: the sieve ------------------------------------------------------
+
+@pytest.mark.parametrize("y1,length", [
+    (1, 3 * TILE + 1234),
+    (10**6 + 3, 2 * TILE + 17),
+    (10**9 - 5, TILE + 1),
+    (10**12 + 12345, 2 * TILE + 999),
+    (2**40 - 1000, TILE + 31),
+    (999_983 * 999_983 - 300, 700),     # a prime square inside the window
+    (1, 1), (2, 5), (7, 60),            # tiny windows
+])
+def test_sieve_mu_matches_oracle(y1, length):
+    mu = torch.empty(length + 16, dtype=torch.int8, device="cuda")
+    pm.mertens_sieve_mu(y1, length, mu)
+    torch.cuda.synchronize()
+    got = mu[:length].cpu().numpy()
+    ref = oracle.mu_window(y1, length)
+    bad = np.nonzero(got != ref)[0]
+    assert bad.size == 0, f"first mismatch at y={y1 + bad[0]}: {got[bad[0]]} vs {ref[bad[0]]}"
+
+
+def test_sieve_M_from_one_matches_table():
+    length = 5 * 10**6 + 7
+    M = torch.empty(length, dtype=torch.int32, device="cuda")
+    pm.mertens_sieve_M(1, length, 0, M)
+    ref = oracle.mertens_table(length)[1:]
+    assert np.array_equal(M.cpu().numpy(), ref)
+
+
+def test_sieve_M_with_carry_far_from_one():
+    y1, length = 10**9 + 7, 3 * TILE + 5
+    carry = oracle.mertens(y1 - 1, L=10**6)
+    M = torch.empty(length, dtype=torch.int32, device="cuda")
+    pm.mertens_sieve_M(y1, length, carry, M)
+    ref = carry + np.cumsum(oracle.mu_window(y1, length).astype(np.int64))
+    assert np.array_equal(M.cpu().numpy().astype(np.int64), ref)
+
+
+def test_sieve_rejects_bad_arguments():
+    mu = torch.empty(64, dtype=torch.int8, device="cuda")
+    with pytest.raises(pm.MertensError):
+        pm.mertens_sieve_mu(0, 10, mu)
+    with pytest.raises(pm.MertensError):
+        pm.mertens_sieve_mu(1, 10, mu.data_ptr() + 1)   # not 16-byte aligned
+
+
+# ---- a1..a4: whole arrays ---------------------------------------------------
+
+def test_every_small_n_every_u():
+    M = oracle.mertens_table(2000)
+    for n in range(1, 121):
+        us = [1] if n == 1 else range(math.isqrt(n) + 1, n + 1)
+        for u in us:
+            m, arr = gpu_array(n, u)
+            X = n // u
+            x = np.arange(1, X + 1)
+            assert m == M[n]
+            assert np.array_equal(arr, M[n // x].astype(np.int64)), (n, u)
+
+
+def test_small_n_auto_parameters_and_tiny_blocks():
+    M = oracle.mertens_table(20000)
+    for n in list(range(1, 400, 7)) + [4096, 4097, 8191, 12288, 19999]:
+        m, arr = gpu_array(n)
+        assert m == M[n], n
+        for bl in (1, 3, 64):
+            if n <= 2000:
+                m2, arr2 = gpu_array(n, 0, bl)
+                assert m2 == M[n] and np.array_equal(arr, arr2), (n, bl)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_random_cases_against_recursion(seed):
+    for n, u, bl in workloads.random_small_cases(seed, 25, 10**10):
+        m, arr = gpu_array(n, u, bl)
+        X = n // u
+        ref = oracle.mertens_array(n, X, L=min(max(math.isqrt(n), 10**6), 10**7))
+        assert np.array_equal(arr, ref), (n, u, bl)
+
+
+def test_config_1e12_full_array():
+    cfg = workloads.SINGLE_1E12
+    n, u, L = cfg["n"][0], cfg["u"], cfg["block_len"]
+    m, arr = gpu_array(n, u, L)
+    ref = oracle.mertens_array(n, n // u, L=10**8)
+    assert np.array_equal(arr, ref)
+
+
+def test_1e9_same_code_path_vs_brute_force_table():
+    n = 10**9
+    m, arr = gpu_array(n, 4 * 10**6, 1 << 20)
+    M = oracle.mertens_table(40_000_000)
+    # entries x >= 25 have k <= 4e7: compare them with the plain table
+    x = np.arange(25, len(arr) + 1)
+    assert np.array_equal(arr[24:], M[n // x].astype(np.int64))
+    assert m == oracle.mertens(n, L=10**7)
+
+
+def test_sec1_extreme_ratio_value():
+    n = 7766842813
+    m, _ = gpu_array(n)
+    assert abs(m) == 50286 and m == oracle.mertens(n, L=10**7)
+
+
+def test_dense_cutoff_does_not_change_results():
+    n, u = 10**11 + 7, 3 * 10**7
+    ref = oracle.mertens_array(n, n // u, L=10**7)
+    old = os.environ.get("MERTENS_DENSE_C")
+    try:
+        for c in ("1.0", "1.6", "3.0", "7.5"):
+            os.environ["MERTENS_DENSE_C"] = c
+            _, arr = gpu_array(n, u, 1 << 22)
+            assert np.array_equal(arr, ref), c
+    finally:
+        if old is None:
+            os.environ.pop("MERTENS_DENSE_C", None)
+        else:
+            os.environ["MERTENS_DENSE_C"] = old
+
+
+def test_batch_same_alone_and_in_mix():
+    ns = [10**12 + i * 10**6 + (i * 7919) % 1000 for i in range(8)] + [10**9 + 1, 12345]
+    plan = pm.mertens_plan(ns)
+    try:
+        pm.mertens_run(plan)
+        mixed = [pm.mertens_result(plan, i, entries=True) for i in range(len(ns))]
+        infos = [pm.mertens_plan_info(plan, i) for i in range(len(ns))]
+    finally:
+        pm.mertens_destroy(plan)
+    for n, (m, arr), info in zip(ns, mixed, infos):
+        m1, arr1 = gpu_array(n, info["u"])
+        assert m == m1 and np.array_equal(arr, arr1), n
+    for i in (0, 7, 8, 9):
+        n = ns[i]
+        ref = oracle.mertens_array(n, infos[i]["X"], L=10**8 if n > 10**10 else 0)
+        assert np.array_equal(mixed[i][1], ref), n
+
+
+def test_run_twice_same_plan():
+    plan = pm.mertens_plan([10**11])
+    try:
+        pm.mertens_run(plan)
+        a = pm.mertens_result(plan, 0, entries=True)
+        pm.mertens_run(plan)
+        b = pm.mertens_result(plan, 0, entries=True)
+    finally:
+        pm.mertens_destroy(plan)
+    assert a[0] == b[0] and np.array_equal(a[1], b[1])
+
+
+def test_result_before_run_is_not_ready():
+    plan = pm.mertens_plan([1000])
+    try:
+        with pytest.raises(pm.MertensError) as ei:
+            pm.mertens_result(plan, 0)
+        assert ei.value.code == pm.MERTENS_ENOTREADY
+        with pytest.raises(pm.MertensError):
+            pm.mertens_result(plan, 1)
+    finally:
+        pm.mertens_destroy(plan)
+
+
+# ---- full size: n = 10^16, u = 4e10, block 2^28 ------------------------------
+
+def test_table1_1e16_full_configuration(table1):
+    cfg = workloads.SINGLE_1E16
+    n, u, L = cfg["n"][0], cfg["u"], cfg["block_len"]
+    m, arr = gpu_array(n, u, L)
+    assert m == table1[10**16] == -3195437
+    # sampled entries: k = floor(n/x) <= 1e11, each by the oracle recursion
+    rng = np.random.default_rng(16)
+    for x in sorted(rng.integers(100_000, len(arr) + 1, size=6)) + [len(arr)]:
+        k = n // int(x)
+        assert arr[int(x) - 1] == oracle.mertens(k, L=10**7), x
