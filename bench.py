@@ -237,7 +237,7 @@ def run_native(args, world, rank, local):
     info = pm.mertens_plan_info(plan, 0)
     terms = info["direct_terms"] + info["gathered_terms"]
     # warm-up (first run also builds the n-independent divisor table)
-    for _ in range(max(args.warmup, 0)):
+    for _ in range(max(args.warmup, 1)):
         pm.mertens_run(plan, stream)
     m_n, _ = pm.mertens_result(plan, 0)
     if cfg["pin"] is not None and m_n != cfg["pin"]:
@@ -272,7 +272,7 @@ def run_native(args, world, rank, local):
     out_np = host_out.numpy()
     e2e_ms = []
     h2d = d2h = 0
-    for it in range(args.e2e_steps + 1):
+    for it in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         p2 = pm.mertens_plan(n_list, u, L)
@@ -285,8 +285,8 @@ def run_native(args, world, rank, local):
         if it > 0:  # first iteration warms the allocator cache
             e2e_ms.append(dt * 1e3)
         h2d, d2h = st2["h2d_bytes"] + 16 * len(n_list), st2["d2h_bytes"]
-    e2e_ms_max = max_over_ranks(float(np.mean(e2e_ms)), world)
-    e2e_value = terms * world / (e2e_ms_max / 1e3)
+    e2e_ms_max = max_over_ranks(float(np.mean(e2e_ms)), world) if e2e_ms else float("nan")
+    e2e_value = terms * world / (e2e_ms_max / 1e3) if e2e_ms else None
 
     # roofline of the dominant kernel class
     peaks, peak_src = load_peaks()

@@ -6,25 +6,36 @@
 
 namespace mert {
 
-// Sieve tile: y values per CTA tile of mu_sieve / m_scan (32-bit smem words).
-constexpr int kSieveTile = 32768;
+// Sieve tile: y values per CTA of the fused mu_sieve / m_scan kernel.  Each
+// y owns a 16-bit half of a 32-bit shared word (two y per word).
+constexpr int kSieveTile = 65536;
+constexpr int kSieveWords = kSieveTile / 2;
 constexpr int kSieveThreads = 1024;
+// M(y) is stored as an int16 relative to M(segment start - 1), one int64
+// offset per segment of kSegY y (|relative M| <= 3/4 kSegY < 2^15).  A
+// segment is the 2048 y one warp of the sieve decodes.
+constexpr int kSegShift = 11;
+constexpr int kSegY = 1 << kSegShift;
 // Dense chunk: y values per chunk of the squarefree list used by the dense
 // update, and the largest number of squarefree y a chunk can hold (one y in
 // four is a multiple of 4, so at most 3/4 of any 4096 consecutive y).
 constexpr int kChunk = 4096;
 constexpr int kChunkCap = 3072;
-// Gathered terms per warp work item.
+// Gathered terms per warp work item of the global-memory gather path.
 constexpr int kSparseItem = 1024;
+// y values per shared-memory tile of the gather path (int16 relative M).
+constexpr int kGatherTile = 32768;
 
-// Fixed-point scale of the log sieve: lg(p) = round(16 * log2 p).
-constexpr int kLogScale = 16;
-// Word layout of the log sieve: bits 0..10 sum of lg(p), bits 11..15 number
-// of distinct sieving primes, bits 16..31 number of sieving-prime squares.
-constexpr uint32_t kCountOne = 1u << 11;
-constexpr uint32_t kSquareOne = 1u << 16;
+// Fixed-point scale of the log sieve: lg(p) = round(8 * log2 p).
+constexpr int kLogScale = 8;
+// Half-word layout of the log sieve: bits 0..9 sum of lg(p) over the distinct
+// sieving primes of y, bits 10..13 their number, bit 15 set when the square
+// of a sieving prime divides y (atomicOr, so it never carries).
+constexpr uint32_t kCountOne = 1u << 10;
+constexpr uint32_t kSquareBit = 1u << 15;
 // Pre-sieve pattern: primes 2,3,5,7 and their squares, period 4*9*25*49.
 constexpr uint32_t kPatternPeriod = 44100;
+constexpr uint32_t kPatternWords = kPatternPeriod / 2;
 
 // Error bits of the plan's device status word.
 constexpr uint32_t kErrMOverflow = 1u;   // |M(y)| did not fit int32

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/libmertens.h"
+#include "common.cuh"
 
 namespace mert {
 
@@ -22,31 +23,32 @@ void dev_free(const Allocator &a, void *p, size_t bytes);
 // Prime table of a plan (device arrays, index 0..np-1, primes ascending,
 // the first four are 2, 3, 5, 7 which the pre-sieve pattern covers).
 struct PrimeTable {
-    uint32_t np = 0;             // primes in the table
-    uint32_t *p = nullptr;       // prime
-    uint32_t *lg = nullptr;      // round(16 * log2 p)
-    uint64_t *m = nullptr;       // division magic of p
-    uint8_t *l = nullptr;        // division shift of p
-    uint32_t *blk_r = nullptr;   // per block: y1 mod p
-    uint32_t *blk_qm = nullptr;  // per block: floor(y1 / p) mod p
-    uint32_t *pattern = nullptr; // pre-sieve pattern, period 44100
+    uint32_t np = 0;              // primes in the table
+    uint32_t *p = nullptr;        // prime
+    uint32_t *lg = nullptr;       // round(8 * log2 p)
+    uint64_t *m = nullptr;        // division magic of p
+    uint8_t *l = nullptr;         // division shift of p
+    uint32_t *blk_r = nullptr;    // per block: y1 mod p
+    uint32_t *blk_qm = nullptr;   // per block: floor(y1 / p) mod p
+    uint32_t *pat_even = nullptr; // pre-sieve pattern words for an even phase
+    uint32_t *pat_odd = nullptr;  // ... and for an odd phase
     // host copy of the primes (for counting primes <= a bound)
     uint32_t *host_p = nullptr;
     Allocator al;
 };
 
-// Arguments of one sieve block (steps a1 + a2).
+// Arguments of one sieve block (steps a1 + a2, fused).  Results:
+//   M(y) = segoff[(y - y1) >> kSegShift] + Mloc[y - y1],  y in [y1, y1+len).
 struct SieveLaunch {
-    uint64_t y1 = 0;          // first y of the block (>= 1)
-    uint64_t len = 0;         // y values in the block
-    int8_t *mu = nullptr;     // [len] mu output
-    int8_t *mu_aux = nullptr; // optional copy of mu for y <= aux_end, index y-1
-    uint64_t aux_end = 0;
-    int32_t *M = nullptr;     // [len] M output (nullptr = mu only)
-    int32_t *tile_sum = nullptr; // [tiles] scratch
-    int64_t *tile_off = nullptr; // [tiles] scratch
-    int64_t *carry = nullptr;    // device M(y1-1) in, M(y1+len-1) out
-    uint32_t *err = nullptr;     // device status word
+    uint64_t y1 = 0;             // first y of the block (>= 1)
+    uint64_t len = 0;            // y values in the block
+    int16_t *Mloc = nullptr;     // [len + 1] M relative to its segment
+    int32_t *segsum = nullptr;   // [segments] scratch: mu sum per segment
+    int64_t *segoff = nullptr;   // [segments] M(segment start - 1)
+    const int64_t *carry_in = nullptr;  // device M(y1 - 1)
+    int64_t *carry_out = nullptr;       // device M(y1 + len - 1)
+    int8_t *mu_out = nullptr;    // optional: mu_out[y - mu_base] for y <= mu_end
+    uint64_t mu_base = 0, mu_end = 0;
     cudaEvent_t mid = nullptr;   // if set: recorded after a1 ...
     cudaEvent_t mid2 = nullptr;  // ... and this one before a2 (profiling)
 };
@@ -56,11 +58,15 @@ int prime_table_create(PrimeTable *t, const Allocator &al, uint64_t y_max, cudaS
 void prime_table_destroy(PrimeTable *t);
 // Number of primes in the table that are <= b.
 uint32_t prime_count_upto(const PrimeTable *t, uint64_t b);
-// Enqueues steps a1 (and a2 when L.M != nullptr) for one block.  Returns the
-// number of kernels launched, or -1 on a launch error.
+// Enqueues the fused steps a1 + a2 for one block.  Returns the number of
+// kernels launched, or -1 on a launch error.
 int sieve_block_enqueue(const PrimeTable *t, const SieveLaunch &L, cudaStream_t s);
-// Tiles of a block of `len` y values.
-inline uint64_t sieve_tiles(uint64_t len) { return (len + 32767) / 32768; }
+// Segments of a block of `len` y values.
+inline uint64_t sieve_segments(uint64_t len) { return (len + kSegY - 1) / kSegY; }
+// M(y) of a window as int32 (the step-level entry point); sets *err bit 1 on
+// an int32 overflow.
+int expand_M_enqueue(const int16_t *Mloc, const int64_t *segoff, uint64_t len, int32_t *M,
+                     uint32_t *err, cudaStream_t s);
 
 // Device-wide exclusive scan of n uint32 values into out[0..n] (out[n] =
 // total).  `scratch` holds at least scan_scratch_words(n) uint32.

@@ -110,9 +110,17 @@ struct mertens_plan_s {
     uint64_t *dK = nullptr, *dJLO = nullptr, *dJC0 = nullptr, *dJCUR = nullptr, *dYCE = nullptr;
     uint64_t *dJTOP = nullptr, *dJBOT = nullptr, *dS = nullptr, *dR = nullptr;
     uint32_t *dICNT = nullptr, *dIOFF = nullptr, *dScan = nullptr;
-    int8_t *dmu_blk = nullptr, *dmu_aux = nullptr;
-    int32_t *dM_blk = nullptr, *dtile_sum = nullptr;
-    int64_t *dtile_off = nullptr, *dcarry = nullptr;
+    int8_t *dmu_aux = nullptr;
+    int16_t *dMloc = nullptr;
+    int32_t *dsegsum = nullptr;
+    int64_t *dsegoff = nullptr, *dcarry = nullptr;
+    // shared-memory gather path: tiles and items of every block, item range
+    // [gblk[b], gblk[b+1]) and last y covered, per block
+    GatherTile *dgtiles = nullptr;
+    GatherItem *dgitems = nullptr;
+    std::vector<uint32_t> gblk;
+    std::vector<uint64_t> gend;
+    uint64_t gather_smem_end = 0;
     uint32_t *derr = nullptr, *dcounter = nullptr;
     uint64_t *dMG = nullptr, *ddl_m = nullptr;
     uint16_t *ddl_yo = nullptr;
@@ -413,6 +421,84 @@ int mertens_plan(mertens_plan_t *out, const mertens_u128 *n, size_t count, merte
     }
     p->nitems = (uint32_t)items.size();
 
+    // ---- shared-memory gather tiles: y in [block start, min(block end, Y_s)]
+    // of each block, items of up to 1024 entries of one target whose dense
+    // cut-off is below the tile end (a suffix of the target's entries, found
+    // on the running minimum of the cut-offs) ----
+    std::vector<uint64_t> ycmin(YCE.size());
+    std::vector<double> kpre(YCE.size() + 1, 0.0);  // prefix sums of k over all entries
+    for (size_t e = 0; e < K.size(); ++e)
+        kpre[e + 1] = kpre[e] + (double)K[e];
+    for (size_t i = 0; i < count; ++i) {
+        uint64_t run = UINT64_MAX;
+        for (uint64_t x = 0; x < p->X[i]; ++x) {
+            run = std::min(run, YCE[p->off[i] + x]);
+            ycmin[p->off[i] + x] = run;
+        }
+    }
+    const double kItemWork = 2.0e5;
+    {
+        const char *e = getenv("MERTENS_GATHER_END");
+        uint64_t ys = e ? strtoull(e, nullptr, 10) : (1ull << 28);
+        p->gather_smem_end = std::min(ys, p->y_max);
+    }
+    std::vector<GatherTile> gtiles;
+    std::vector<GatherItem> gitems;
+    for (uint64_t b = 0; b < p->nblocks; ++b) {
+        const uint64_t y1 = 1 + b * block_len;
+        const uint64_t y2 = std::min(y1 + block_len - 1, p->y_max);
+        p->gblk.push_back((uint32_t)gitems.size());
+        const uint64_t end = std::min(y2, p->gather_smem_end);
+        p->gend.push_back(y1 <= end ? end : y1 - 1);
+        for (uint64_t t1 = y1; t1 <= end; t1 += kGatherTile) {
+            const uint64_t t2 = std::min(t1 + kGatherTile - 1, end);
+            GatherTile T;
+            T.t1 = t1;
+            T.len = (uint32_t)(t2 - t1 + 1);
+            T.m1 = magic_of(t1);
+            T.l1 = magic_shift(t1);
+            T.m2 = magic_of(t2 + 1);
+            T.l2 = magic_shift(t2 + 1);
+            T.pad = 0;
+            const uint32_t ti = (uint32_t)gtiles.size();
+            bool used = false;
+            for (size_t i = 0; i < count; ++i) {
+                const uint64_t o = p->off[i], X = p->X[i];
+                uint64_t lo = 0, hi = X;  // first x index with ycmin < t2
+                while (lo < hi) {
+                    const uint64_t mid = (lo + hi) / 2;
+                    if (ycmin[o + mid] < t2)
+                        hi = mid;
+                    else
+                        lo = mid + 1;
+                }
+                // work of entries [f, g): about one range check each plus
+                // sum k * len / t1^2 gathered terms; items of ~kItemWork
+                const double per_k = (double)T.len / ((double)t1 * (double)t1);
+                for (uint64_t f = lo; f < X;) {
+                    uint64_t g = std::min<uint64_t>(f + 1024, X);
+                    while (g < X) {
+                        const double work = (double)(g - f) + per_k * (kpre[o + g] - kpre[o + f]);
+                        if (work >= kItemWork)
+                            break;
+                        g = std::min<uint64_t>(g + 1024, X);
+                    }
+                    GatherItem it;
+                    it.tile = ti;
+                    it.e0 = (uint32_t)(o + f);
+                    it.e1 = (uint32_t)(o + g);
+                    it.pad = 0;
+                    gitems.push_back(it);
+                    used = true;
+                    f = g;
+                }
+            }
+            if (used)
+                gtiles.push_back(T);
+        }
+    }
+    p->gblk.push_back((uint32_t)gitems.size());
+
     // ---- device buffers ----
     int rc = MERTENS_OK;
     const size_t E = p->nent;
@@ -429,13 +515,15 @@ int mertens_plan(mertens_plan_t *out, const mertens_u128 *n, size_t count, merte
     p->dIOFF = p->alloc<uint32_t>(E + 1);
     p->dScan = p->alloc<uint32_t>(scan_scratch_words(E));
     const uint64_t L = block_len;
-    const uint64_t tiles = sieve_tiles(L);
-    p->dmu_blk = p->alloc<int8_t>(((L + 15) / 16) * 16);
+    const uint64_t nseg = sieve_segments(L);
     p->dmu_aux = p->alloc<int8_t>(p->ydense + 16);
-    p->dM_blk = p->alloc<int32_t>(L);
-    p->dtile_sum = p->alloc<int32_t>(tiles);
-    p->dtile_off = p->alloc<int64_t>(tiles);
-    p->dcarry = p->alloc<int64_t>(1);
+    p->dMloc = p->alloc<int16_t>(L + 2);
+    p->dsegsum = p->alloc<int32_t>(nseg);
+    p->dsegoff = p->alloc<int64_t>(nseg);
+    p->dcarry = p->alloc<int64_t>(p->nblocks + 1);
+    p->dgtiles = p->alloc<GatherTile>(gtiles.size() + 1);
+    p->dgitems = p->alloc<GatherItem>(gitems.size() + 1);
+
     p->derr = p->alloc<uint32_t>(1);
     p->dcounter = p->alloc<uint32_t>(1);
     p->dMG = p->alloc<uint64_t>(p->mg_n + 1);
@@ -450,8 +538,8 @@ int mertens_plan(mertens_plan_t *out, const mertens_u128 *n, size_t count, merte
             rc = MERTENS_ENOMEM;
     bool any_null = !p->dK || !p->dJLO || !p->dJC0 || !p->dJCUR || !p->dYCE || !p->dJTOP ||
                     !p->dJBOT || !p->dS || !p->dR || !p->dICNT || !p->dIOFF || !p->dScan ||
-                    !p->dmu_blk || !p->dmu_aux || !p->dM_blk || !p->dtile_sum ||
-                    !p->dtile_off || !p->dcarry || !p->derr || !p->dcounter || !p->dMG ||
+                    !p->dmu_aux || !p->dMloc || !p->dsegsum || !p->dsegoff || !p->dgtiles ||
+                    !p->dgitems || !p->dcarry || !p->derr || !p->dcounter || !p->dMG ||
                     !p->ddl_m || !p->ddl_yo || !p->ddl_cnt || !p->dgroups || !p->ditems ||
                     !p->dqs;
     if (any_null)
@@ -476,8 +564,15 @@ int mertens_plan(mertens_plan_t *out, const mertens_u128 *n, size_t count, merte
             cudaMemcpy(p->ditems, items.data(), items.size() * sizeof(DenseItem),
                        cudaMemcpyHostToDevice);
         cudaMemcpy(p->dqs, qs.data(), count * sizeof(QueryDev), cudaMemcpyHostToDevice);
+        if (!gtiles.empty())
+            cudaMemcpy(p->dgtiles, gtiles.data(), gtiles.size() * sizeof(GatherTile),
+                       cudaMemcpyHostToDevice);
+        if (!gitems.empty())
+            cudaMemcpy(p->dgitems, gitems.data(), gitems.size() * sizeof(GatherItem),
+                       cudaMemcpyHostToDevice);
         p->h2d_bytes = 4 * E * 8 + sg.size() * sizeof(Group) + items.size() * sizeof(DenseItem) +
-                       count * sizeof(QueryDev);
+                       count * sizeof(QueryDev) + gtiles.size() * sizeof(GatherTile) +
+                       gitems.size() * sizeof(GatherItem);
         if (cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming) != cudaSuccess ||
             cudaGetLastError() != cudaSuccess)
             rc = MERTENS_ECUDA;
@@ -536,7 +631,7 @@ int mertens_run(mertens_plan_t p, void *stream)
     const size_t E = p->nent;
     cudaMemsetAsync(p->dS, 0, E * 8, s);
     cudaMemcpyAsync(p->dJCUR, p->dJC0, E * 8, cudaMemcpyDeviceToDevice, s);
-    cudaMemsetAsync(p->dcarry, 0, 8, s);
+    cudaMemsetAsync(p->dcarry, 0, 8 * (p->nblocks + 1), s);
     cudaMemsetAsync(p->derr, 0, 4, s);
     if (!p->mg_built) {
         r = magic_table_enqueue(p->dMG, p->mg_n, s);
@@ -553,14 +648,14 @@ int mertens_run(mertens_plan_t p, void *stream)
             SieveLaunch L;
             L.y1 = y1;
             L.len = y2 - y1 + 1;
-            L.mu = p->dmu_blk;
-            L.mu_aux = (y1 <= p->ydense) ? p->dmu_aux : nullptr;
-            L.aux_end = p->ydense;
-            L.M = p->dM_blk;
-            L.tile_sum = p->dtile_sum;
-            L.tile_off = p->dtile_off;
-            L.carry = p->dcarry;
-            L.err = p->derr;
+            L.Mloc = p->dMloc;
+            L.segsum = p->dsegsum;
+            L.segoff = p->dsegoff;
+            L.carry_in = p->dcarry + b;
+            L.carry_out = p->dcarry + b + 1;
+            L.mu_out = (y1 <= p->ydense) ? p->dmu_aux : nullptr;
+            L.mu_base = 1;
+            L.mu_end = p->ydense;
             PhaseEvents pe, pe2;
             ev_begin(p, kPhSieve, s, &pe);
             if (p->prof) {
@@ -624,7 +719,32 @@ int mertens_run(mertens_plan_t p, void *stream)
             sa.S = p->dS;
             sa.ICNT = p->dICNT;
             sa.IOFF = p->dIOFF;
-            sa.Mblk = p->dM_blk;
+            sa.Mloc = p->dMloc;
+            sa.segoff = p->dsegoff;
+            sa.y_lo = p->gend[b] + 1 > y1 ? p->gend[b] + 1 : y1;
+            sa.m_ylo = magic_of(sa.y_lo);
+            sa.l_ylo = magic_shift(sa.y_lo);
+            if (p->gblk[b + 1] > p->gblk[b]) {
+                GatherArgs ga;
+                ga.y1 = y1;
+                ga.tiles = p->dgtiles;
+                ga.items = p->dgitems + p->gblk[b];
+                ga.nitems = p->gblk[b + 1] - p->gblk[b];
+                ga.counter = p->dcounter;
+                ga.Mloc = p->dMloc;
+                ga.segoff = p->dsegoff;
+                ga.K = p->dK;
+                ga.JLO = p->dJLO;
+                ga.JCUR = p->dJCUR;
+                ga.MG = p->dMG;
+                ga.S = p->dS;
+                ev_begin(p, kPhGather, s, &pe);
+                r = gather_tiles_enqueue(ga, s);
+                ev_end(p, s, &pe);
+                if (r < 0)
+                    goto fail;
+                launches += r;
+            }
             ev_begin(p, kPhGather, s, &pe);
             r = sparse_block_enqueue(sb, sa, p->dScan, s);
             ev_end(p, s, &pe);
@@ -795,19 +915,14 @@ static int sieve_window(uint64_t y1, uint64_t len, int8_t *mu_dev, int64_t carry
             prime_table_destroy(&pt);
         return prc == 6 ? MERTENS_ENOTSUP : (prc == 2 ? MERTENS_ENOMEM : MERTENS_ECUDA);
     }
-    const uint64_t tiles = sieve_tiles(len);
-    int8_t *mu = mu_dev;
-    bool own_mu = false;
-    if (!mu) {
-        mu = (int8_t *)dev_alloc(al, ((len + 15) / 16) * 16);
-        own_mu = true;
-    }
-    int32_t *ts = (int32_t *)dev_alloc(al, tiles * 4);
-    int64_t *to = (int64_t *)dev_alloc(al, tiles * 8);
-    int64_t *cy = (int64_t *)dev_alloc(al, 8);
+    const uint64_t nseg = sieve_segments(len);
+    int16_t *ml = (int16_t *)dev_alloc(al, (len + 2) * 2);
+    int32_t *ss = (int32_t *)dev_alloc(al, nseg * 4);
+    int64_t *so = (int64_t *)dev_alloc(al, nseg * 8);
+    int64_t *cy = (int64_t *)dev_alloc(al, 16);
     uint32_t *er = (uint32_t *)dev_alloc(al, 4);
     int rc = MERTENS_OK;
-    if (!mu || !ts || !to || !cy || !er)
+    if (!ml || !ss || !so || !cy || !er)
         rc = MERTENS_ENOMEM;
     if (rc == MERTENS_OK) {
         cudaMemcpyAsync(cy, &carry, 8, cudaMemcpyHostToDevice, s);
@@ -815,13 +930,17 @@ static int sieve_window(uint64_t y1, uint64_t len, int8_t *mu_dev, int64_t carry
         SieveLaunch L;
         L.y1 = y1;
         L.len = len;
-        L.mu = mu;
-        L.M = M_dev;
-        L.tile_sum = ts;
-        L.tile_off = to;
-        L.carry = cy;
-        L.err = er;
+        L.Mloc = ml;
+        L.segsum = ss;
+        L.segoff = so;
+        L.carry_in = cy;
+        L.carry_out = cy + 1;
+        L.mu_out = mu_dev;
+        L.mu_base = y1;
+        L.mu_end = y1 + len - 1;
         if (sieve_block_enqueue(&pt, L, s) < 0)
+            rc = MERTENS_ECUDA;
+        if (rc == MERTENS_OK && M_dev && expand_M_enqueue(ml, so, len, M_dev, er, s) < 0)
             rc = MERTENS_ECUDA;
         uint32_t e = 0;
         if (cudaMemcpyAsync(&e, er, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -832,11 +951,10 @@ static int sieve_window(uint64_t y1, uint64_t len, int8_t *mu_dev, int64_t carry
     }
     if (rc == MERTENS_ECUDA)
         set_last_error("sieve: %s", cudaGetErrorString(cudaGetLastError()));
-    if (own_mu)
-        dev_free(al, mu, ((len + 15) / 16) * 16);
-    dev_free(al, ts, tiles * 4);
-    dev_free(al, to, tiles * 8);
-    dev_free(al, cy, 8);
+    dev_free(al, ml, (len + 2) * 2);
+    dev_free(al, ss, nseg * 4);
+    dev_free(al, so, nseg * 8);
+    dev_free(al, cy, 16);
     dev_free(al, er, 4);
     prime_table_destroy(&pt);
     return rc;

@@ -1,6 +1,9 @@
-// Steps a1 (mu_sieve) and a2 (m_scan) of the isolated-value Mertens method:
-// mu(y) for a block of y by a segmented log sieve, then M(y) by prefix sum
-// with the carry of the previous block (arXiv:1108.0135, Sec. 3).
+// Steps a1 (mu_sieve) and a2 (m_scan) of the isolated-value Mertens method,
+// fused into one kernel per sieve block: mu(y) by a segmented log sieve, then
+// M(y) by prefix sum (arXiv:1108.0135, Sec. 3, steps 0-5 of the log sieve),
+// stored as int16 relative to M at the start of each kSegY-segment; a second
+// small kernel turns the segment sums into int64 segment offsets carrying
+// M(y1 - 1) from the previous block.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -27,15 +30,16 @@ __global__ void sieve_block_prep_kernel(uint64_t y1, uint32_t np, const uint32_t
 
 struct SieveArgs {
     uint64_t y1, len;
-    uint32_t np, np_small;      // primes used; [4, np_small) sieved warp-cooperatively
-    float thr_bias;             // 8 * log2(P), P = largest value all of whose primes are sieved
-    const uint32_t *p, *lg, *r, *qm, *pattern;
+    uint32_t np, np_small;  // primes used; [4, np_small) sieved warp-cooperatively
+    uint32_t np_quarter;    // [4, np_quarter) sieved in quarter-tile pieces
+    float thr_bias;         // (kLogScale/2) * log2(P), all primes <= P sieved
+    const uint32_t *p, *lg, *r, *qm, *pat_even, *pat_odd;
     const uint64_t *m;
     const uint8_t *l;
-    int8_t *mu;
-    int8_t *mu_aux;
-    uint64_t aux_end;
-    int32_t *tile_sum;
+    int16_t *Mloc;
+    int32_t *segsum;
+    int8_t *mu_out;
+    uint64_t mu_base, mu_end;
 };
 
 // First multiple of p at or after t1 = y1 + a0, as an offset `off` into the
@@ -47,7 +51,7 @@ __device__ __forceinline__ void first_multiple(const SieveArgs &a, uint32_t t, u
     p = a.p[t];
     const uint64_t m = a.m[t];
     const unsigned l = a.l[t];
-    const uint64_t v = (uint64_t)a.r[t] + a0;       // (t1 - floor(y1/p)*p)
+    const uint64_t v = (uint64_t)a.r[t] + a0;       // t1 - floor(y1/p)*p
     const uint64_t qv = div_magic(v << 1, m, l);     // floor(v / p)
     const uint32_t off0 = (uint32_t)(v - qv * p);    // t1 mod p
     off = off0 ? p - off0 : 0u;
@@ -55,179 +59,254 @@ __device__ __forceinline__ void first_multiple(const SieveArgs &a, uint32_t t, u
     c = (uint32_t)(c0 - div_magic(c0 << 1, m, l) * p);
 }
 
-// mu(y) for one tile of kSieveTile y values.  Each y owns one 32-bit shared
-// word; every sieving prime p adds round(16 log2 p) plus one to the prime
-// count at its multiples, and one to the square count at multiples of p^2
-// (shared-memory atomics).  Primes 2, 3, 5, 7 and their squares come from a
-// periodic pattern.  Decoding (exact; proof in the design notes): with all
-// primes <= P sieved and (P+1)^2 > y, the unsieved cofactor c of y is 1 or a
-// prime > P; the log sum A is within 7.5 units of 16 log2 y when c = 1 and at
-// least 16 log2 P - 7 units below it otherwise, so "A > 16 log2 y - 8 log2 P"
-// decides c = 1.  mu = 0 if a square divides y, else (-1)^(count + [c > 1]).
-__global__ void __launch_bounds__(kSieveThreads) mu_sieve_kernel(SieveArgs a)
+// mu of one sieve half-word h given the integer threshold ithr (see below).
+__device__ __forceinline__ int decode_mu(uint32_t h, int ithr)
 {
-    extern __shared__ uint32_t w[];
-    __shared__ int red[33];
+    const int A = (int)(h & 1023u);
+    const int cnt = (int)((h >> 10) & 15u);
+    const int extra = A > ithr ? 0 : 1;  // 1: one prime factor above P remains
+    const int mu = ((cnt + extra) & 1) ? -1 : 1;
+    return (h & kSquareBit) ? 0 : mu;
+}
+
+// floor(8 log2 y - 4 log2 P): A exceeds it exactly when the sieved primes
+// account for all of y.
+__device__ __forceinline__ int thr_of(uint64_t y, float bias)
+{
+    return (int)floorf((float)kLogScale * __log2f(__ull2float_rn(y)) - bias);
+}
+
+// Multiples of prime t in the tile offsets [lo, hi), lanes over them.
+__device__ __forceinline__ void sieve_prime_warp(const SieveArgs &a, uint32_t *w, uint32_t t,
+                                                 uint64_t a0, uint32_t lo, uint32_t hi, int lane)
+{
+    uint32_t p, off, c;
+    first_multiple(a, t, a0, p, off, c);
+    if (off < lo) {
+        const uint32_t steps = (lo - off + p - 1) / p;
+        off += steps * p;
+        c = (c + steps) % p;
+    }
+    const uint32_t add = a.lg[t] | kCountOne;
+    uint32_t ci = (c + (uint32_t)lane) % p;
+    const uint32_t inc = 32u % p;
+    for (uint32_t yo = off + (uint32_t)lane * p; yo < hi; yo += 32u * p) {
+        const uint32_t sh = (yo & 1u) << 4;
+        atomicAdd(&w[yo >> 1], add << sh);
+        if (ci == 0)
+            atomicOr(&w[yo >> 1], kSquareBit << sh);
+        ci += inc;
+        if (ci >= p)
+            ci -= p;
+    }
+}
+
+// One tile of kSieveTile y.  Shared half-word per y: every sieving prime p
+// adds round(8 log2 p) plus one to the prime count at its multiples and sets
+// the square bit at multiples of p^2; primes 2, 3, 5, 7 and their squares come
+// from a periodic pattern.  Decoding is exact: with all primes <= P sieved and
+// (P+1)^2 > y, the unsieved cofactor c of y is 1 or a prime > P.  The log sum
+// A is within 7.5 units of 8 log2 y when c = 1 (at most 15 distinct primes,
+// each rounded by <= 1/2) and at least 8 log2(P+1) - 7 units below it
+// otherwise, so "A > 8 log2 y - 4 log2 P" decides c = 1 for every P >= 7
+// (margins >= 3.7 units).  mu = 0 if the square bit is set, else
+// (-1)^(count + [c > 1]).  Each warp then turns its 2048 y (one segment)
+// into M relative to the segment start with a warp scan.
+//
+// Sieving work is handed out to warps through a shared counter, largest jobs
+// first: primes below 128 in quarter-tile pieces, the other primes below 2048
+// one per warp (lanes over multiples), then the larger primes 32 at a time
+// (a lane per prime).
+__global__ void __launch_bounds__(kSieveThreads, 1) mu_sieve_kernel(SieveArgs a)
+{
+    extern __shared__ uint32_t w[];  // kSieveWords words, two y each
+    __shared__ uint32_t s_job;
     const uint64_t a0 = (uint64_t)blockIdx.x * kSieveTile;
     const uint64_t t1 = a.y1 + a0;
     const uint32_t tl = (uint32_t)((a.len - a0) < (uint64_t)kSieveTile ? (a.len - a0) : kSieveTile);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-    // pattern of primes 2,3,5,7 (period 44100 > tile, so at most one wrap)
+    // pattern of primes 2, 3, 5, 7 and their squares
     {
         const uint32_t ph = (uint32_t)(t1 % kPatternPeriod);
-        for (uint32_t i = threadIdx.x; i < (uint32_t)kSieveTile; i += blockDim.x) {
-            uint32_t idx = ph + i;
-            if (idx >= kPatternPeriod)
-                idx -= kPatternPeriod;
-            w[i] = a.pattern[idx];
+        const uint32_t *pat = (ph & 1u) ? a.pat_odd : a.pat_even;
+        const uint32_t j0 = ph >> 1;
+        for (uint32_t i = threadIdx.x; i < (uint32_t)kSieveWords; i += kSieveThreads) {
+            uint32_t idx = j0 + i;
+            if (idx >= kPatternWords)
+                idx -= kPatternWords;
+            if (idx >= kPatternWords)
+                idx -= kPatternWords;
+            w[i] = pat[idx];
         }
+        if (threadIdx.x == 0)
+            s_job = 0;
     }
     __syncthreads();
 
-    // small primes: a warp per prime, lanes over its multiples
-    for (uint32_t t = 4 + warp; t < a.np_small; t += nwarp) {
-        uint32_t p, off, c;
-        first_multiple(a, t, a0, p, off, c);
-        const uint32_t add = a.lg[t] | kCountOne;
-        uint32_t ci = (c + (uint32_t)lane) % p;
-        const uint32_t inc = 32u % p;
-        for (uint32_t yo = off + (uint32_t)lane * p; yo < tl; yo += 32u * p) {
-            atomicAdd(&w[yo], add + (ci == 0 ? kSquareOne : 0u));
-            ci += inc;
-            if (ci >= p)
-                ci -= p;
-        }
-    }
-    // large primes: a thread per prime
-    for (uint32_t t = (a.np_small > 4 ? a.np_small : 4) + threadIdx.x; t < a.np; t += blockDim.x) {
-        uint32_t p, off, c;
-        first_multiple(a, t, a0, p, off, c);
-        const uint32_t add = a.lg[t] | kCountOne;
-        for (uint32_t yo = off; yo < tl; yo += p) {
-            atomicAdd(&w[yo], add + (c == 0 ? kSquareOne : 0u));
-            c = (c + 1 == p) ? 0u : c + 1;
-        }
-    }
-    __syncthreads();
-
-    // decode 16 consecutive y per step, 16-byte stores
-    int sum = 0;
-    const uint32_t ngroups = (tl + 15) / 16;
-    for (uint32_t g = threadIdx.x; g < ngroups; g += blockDim.x) {
-        const uint32_t i0 = g * 16;
-        const uint64_t y0 = t1 + i0;
-        const float base = (float)kLogScale * __log2f(__ull2float_rn(y0)) - a.thr_bias;
-        int8_t v[16];
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            const uint32_t word = w[(i0 + k) < (uint32_t)kSieveTile ? i0 + k : 0];
-            const uint64_t y = y0 + k;
-            float thr = base;
-            if (y0 < 4096)
-                thr = (float)kLogScale * __log2f((float)y) - a.thr_bias;
-            const int A = (int)(word & 2047u);
-            const int cnt = (int)((word >> 11) & 31u);
-            const int fully = (float)A > thr ? 1 : 0;
-            int mu = ((cnt + (fully ^ 1)) & 1) ? -1 : 1;
-            if (word >> 16)
-                mu = 0;
-            v[k] = (int8_t)((i0 + k) < tl ? mu : 0);
-            sum += v[k];
-        }
-        int8_t *dst = a.mu + a0 + i0;
-        if (i0 + 16 <= tl) {
-            int4 pack;
-            memcpy(&pack, v, 16);
-            *reinterpret_cast<int4 *>(dst) = pack;
+    const uint32_t nquart = a.np_quarter > 4 ? a.np_quarter - 4 : 0;  // primes 11..127
+    const uint32_t jq = 4 * nquart;
+    const uint32_t js = jq + (a.np_small > a.np_quarter ? a.np_small - a.np_quarter : 0);
+    const uint32_t nlarge = a.np > a.np_small ? a.np - a.np_small : 0;
+    const uint32_t jobs = js + (nlarge + 31) / 32;
+    for (;;) {
+        uint32_t job = 0;
+        if (lane == 0)
+            job = atomicAdd(&s_job, 1u);
+        job = __shfl_sync(0xffffffffu, job, 0);
+        if (job >= jobs)
+            break;
+        if (job < jq) {
+            const uint32_t q = job & 3u;
+            const uint32_t lo = q * (kSieveTile / 4), hi = min(tl, (q + 1) * (kSieveTile / 4));
+            if (lo < hi)
+                sieve_prime_warp(a, w, 4 + (job >> 2), a0, lo, hi, lane);
+        } else if (job < js) {
+            sieve_prime_warp(a, w, a.np_quarter + (job - jq), a0, 0, tl, lane);
         } else {
-            for (uint32_t k = 0; i0 + k < tl; ++k)
-                dst[k] = v[k];
-        }
-        if (a.mu_aux && y0 <= a.aux_end) {
-            for (int k = 0; k < 16; ++k) {
-                const uint64_t y = y0 + k;
-                if (i0 + k < tl && y <= a.aux_end)
-                    a.mu_aux[y - 1] = v[k];
+            const uint32_t t = a.np_small + (job - js) * 32u + (uint32_t)lane;
+            if (t < a.np) {
+                uint32_t p, off, c;
+                first_multiple(a, t, a0, p, off, c);
+                const uint32_t add = a.lg[t] | kCountOne;
+                for (uint32_t yo = off; yo < tl; yo += p) {
+                    const uint32_t sh = (yo & 1u) << 4;
+                    atomicAdd(&w[yo >> 1], add << sh);
+                    if (c == 0)
+                        atomicOr(&w[yo >> 1], kSquareBit << sh);
+                    c = (c + 1 == p) ? 0u : c + 1;
+                }
             }
         }
     }
-    int tot;
-    block_excl_scan<int>(sum, red, &tot);
-    if (threadIdx.x == 0 && a.tile_sum)
-        a.tile_sum[blockIdx.x] = tot;
+    __syncthreads();
+
+    // decode + scan: warp owns words [wb, wb+1024) = y offsets [2wb, 2wb+2048)
+    const uint32_t wb = (uint32_t)warp * 1024u;
+    const uint32_t so = 2u * wb;  // segment start within the tile
+    if (so >= tl)
+        return;
+    const uint64_t ys = t1 + so;
+    const bool big = ys >= (1ull << 20);
+    const int thw = big ? thr_of(ys, a.thr_bias) : 0;  // y varies by < 2^-9 in the segment
+    const bool want_mu = a.mu_out && ys <= a.mu_end && ys + 2047 >= a.mu_base;
+    int run = 0;
+#pragma unroll 1
+    for (int r = 0; r < 8; ++r) {
+        const uint32_t wi = wb + (uint32_t)r * 128u + 4u * (uint32_t)lane;  // 4 words = 8 y
+        const uint4 q4 = *reinterpret_cast<const uint4 *>(w + wi);
+        const uint32_t ws[4] = {q4.x, q4.y, q4.z, q4.w};
+        const uint32_t o0 = 2u * wi;  // tile offset of the first of the 8 y
+        const uint64_t y0 = t1 + o0;
+        int th[8];
+        if (big) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                th[k] = thw;
+        } else if (y0 >= 16384) {
+            const int t0 = thr_of(y0, a.thr_bias);
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                th[k] = t0;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                th[k] = thr_of(y0 + k, a.thr_bias);
+        }
+        int mu[8];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            mu[2 * k] = decode_mu(ws[k] & 0xffffu, th[2 * k]);
+            mu[2 * k + 1] = decode_mu(ws[k] >> 16, th[2 * k + 1]);
+        }
+        if (o0 + 8u > tl) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (o0 + k >= tl)
+                    mu[k] = 0;
+        }
+        int loc[8], sum = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            sum += mu[k];
+            loc[k] = sum;
+        }
+        int inc = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int nb = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o)
+                inc += nb;
+        }
+        const int base = run + inc - sum;
+        run += __shfl_sync(0xffffffffu, inc, 31);
+        if (o0 + 8u <= tl) {
+            uint4 out;
+            out.x = (uint32_t)(uint16_t)(int16_t)(base + loc[0]) |
+                    ((uint32_t)(uint16_t)(int16_t)(base + loc[1]) << 16);
+            out.y = (uint32_t)(uint16_t)(int16_t)(base + loc[2]) |
+                    ((uint32_t)(uint16_t)(int16_t)(base + loc[3]) << 16);
+            out.z = (uint32_t)(uint16_t)(int16_t)(base + loc[4]) |
+                    ((uint32_t)(uint16_t)(int16_t)(base + loc[5]) << 16);
+            out.w = (uint32_t)(uint16_t)(int16_t)(base + loc[6]) |
+                    ((uint32_t)(uint16_t)(int16_t)(base + loc[7]) << 16);
+            *reinterpret_cast<uint4 *>(a.Mloc + a0 + o0) = out;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (o0 + k < tl)
+                    a.Mloc[a0 + o0 + k] = (int16_t)(base + loc[k]);
+        }
+        if (want_mu) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const uint64_t y = y0 + k;
+                if (o0 + k < tl && y >= a.mu_base && y <= a.mu_end)
+                    a.mu_out[y - a.mu_base] = (int8_t)mu[k];
+            }
+        }
+    }
+    if (lane == 0)
+        a.segsum[(a0 + so) >> kSegShift] = run;
 }
 
-// ---------------------------------------------------------------------------
-// a2: carries of the tiles, then M(y) of each tile.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) tile_carry_kernel(const int32_t *__restrict__ tile_sum,
-                                                          uint32_t ntiles,
-                                                          int64_t *__restrict__ tile_off,
-                                                          int64_t *__restrict__ carry)
+// a2 finish: segoff[s] = carry_in + sum of segsum[0..s) (int64), and
+// carry_out = carry_in + all of them.  Each CTA scans 1024 segments and adds
+// the sum of all segments before its range.
+__global__ void __launch_bounds__(1024) seg_carry_kernel(const int32_t *__restrict__ segsum,
+                                                         uint32_t nseg,
+                                                         const int64_t *__restrict__ carry_in,
+                                                         int64_t *__restrict__ segoff,
+                                                         int64_t *__restrict__ carry_out)
 {
     __shared__ int64_t sh[33];
-    const uint32_t per = (ntiles + blockDim.x - 1) / blockDim.x;
-    const uint32_t b = threadIdx.x * per, e = min(ntiles, b + per);
-    int64_t s = 0;
-    for (uint32_t i = b; i < e; ++i)
-        s += tile_sum[i];
+    const uint32_t base = blockIdx.x * 1024u;
+    int64_t before = 0;
+    for (uint32_t i = threadIdx.x; i < base; i += 1024u)
+        before += segsum[i];
+    int64_t tb;
+    block_excl_scan<int64_t>(before, sh, &tb);
+    const uint32_t i = base + threadIdx.x;
+    const int64_t v = i < nseg ? segsum[i] : 0;
     int64_t tot;
-    int64_t ex = block_excl_scan<int64_t>(s, sh, &tot);
-    const int64_t base = *carry;
-    __syncthreads();
-    int64_t run = base + ex;
-    for (uint32_t i = b; i < e; ++i) {
-        tile_off[i] = run;
-        run += tile_sum[i];
-    }
-    if (threadIdx.x == 0)
-        *carry = base + tot;
+    const int64_t ex = block_excl_scan<int64_t>(v, sh, &tot);
+    const int64_t c0 = *carry_in;
+    if (i < nseg)
+        segoff[i] = c0 + tb + ex;
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0)
+        *carry_out = c0 + tb + tot;
 }
 
-// M(y) = carry + prefix sum of mu over one tile: 1024 threads x 32 y, then a
-// padded shared-memory transpose for coalesced int32 stores.
-__global__ void __launch_bounds__(1024) m_scan_kernel(const int8_t *__restrict__ mu, uint64_t len,
-                                                      const int64_t *__restrict__ tile_off,
-                                                      int32_t *__restrict__ M,
-                                                      uint32_t *__restrict__ err)
+__global__ void expand_M_kernel(const int16_t *__restrict__ Mloc, const int64_t *__restrict__ segoff,
+                                uint64_t len, int32_t *__restrict__ M, uint32_t *__restrict__ err)
 {
-    extern __shared__ int32_t buf[];  // kSieveTile + kSieveTile/32 words
-    __shared__ int32_t sh[33];
-    const uint64_t a0 = (uint64_t)blockIdx.x * kSieveTile;
-    const uint32_t tl = (uint32_t)((len - a0) < (uint64_t)kSieveTile ? (len - a0) : kSieveTile);
-    const uint32_t i0 = threadIdx.x * 32;
-    int8_t v[32];
-    if (i0 + 32 <= tl) {
-        const int4 *src = reinterpret_cast<const int4 *>(mu + a0 + i0);
-        int4 x0 = src[0], x1 = src[1];
-        memcpy(v, &x0, 16);
-        memcpy(v + 16, &x1, 16);
-    } else {
-#pragma unroll
-        for (int k = 0; k < 32; ++k)
-            v[k] = (i0 + k < tl) ? mu[a0 + i0 + k] : 0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const int64_t v = segoff[i >> kSegShift] + Mloc[i];
+        if (v > INT32_MAX || v < INT32_MIN)
+            atomicOr(err, kErrMOverflow);
+        M[i] = (int32_t)v;
     }
-    int run = 0;
-#pragma unroll
-    for (int k = 0; k < 32; ++k)
-        run += v[k];
-    int tot;
-    const int ex = block_excl_scan<int>(run, sh, &tot);
-    int64_t mv = tile_off[blockIdx.x] + ex;
-    bool bad = false;
-#pragma unroll
-    for (int k = 0; k < 32; ++k) {
-        mv += v[k];
-        bad |= (mv > INT32_MAX) || (mv < INT32_MIN);
-        const uint32_t e = i0 + k;
-        buf[e + (e >> 5)] = (int32_t)mv;
-    }
-    if (bad)
-        atomicOr(err, kErrMOverflow);
-    __syncthreads();
-    for (uint32_t e = threadIdx.x; e < tl; e += blockDim.x)
-        M[a0 + e] = buf[e + (e >> 5)];
 }
 
 // ---------------------------------------------------------------------------
@@ -250,9 +329,9 @@ static std::vector<uint32_t> host_primes(uint64_t B)
 static uint64_t isqrt_u64(uint64_t v)
 {
     uint64_t r = (uint64_t)std::sqrt((double)v);
-    while (r * r > v)
+    while (r > 0 && r > v / r)
         --r;
-    while ((r + 1) * (r + 1) <= v)
+    while ((r + 1) <= v / (r + 1))
         ++r;
     return r;
 }
@@ -275,19 +354,24 @@ int prime_table_create(PrimeTable *t, const Allocator &al, uint64_t y_max, cudaS
         mg[i] = magic_of(pr[i]);
         sh[i] = (uint8_t)magic_shift(pr[i]);
     }
-    // pattern for 2,3,5,7 and 4,9,25,49
-    std::vector<uint32_t> pat(kPatternPeriod, 0);
+    // half-word pattern for 2,3,5,7 and 4,9,25,49, then the two word tables
+    std::vector<uint32_t> pat16(kPatternPeriod, 0);
     const uint32_t small[4] = {2, 3, 5, 7};
     for (uint32_t i = 0; i < kPatternPeriod; ++i) {
-        uint32_t wv = 0;
+        uint32_t h = 0;
         for (int q = 0; q < 4; ++q) {
             const uint32_t p = small[q];
             if (i % p == 0)
-                wv += lg[q] | kCountOne;
+                h += lg[q] | kCountOne;
             if (i % (p * p) == 0)
-                wv += kSquareOne;
+                h |= kSquareBit;
         }
-        pat[i] = wv;
+        pat16[i] = h;
+    }
+    std::vector<uint32_t> pe(kPatternWords), po(kPatternWords);
+    for (uint32_t j = 0; j < kPatternWords; ++j) {
+        pe[j] = pat16[2 * j] | (pat16[2 * j + 1] << 16);
+        po[j] = pat16[2 * j + 1] | (pat16[(2 * j + 2) % kPatternPeriod] << 16);
     }
     t->np = (uint32_t)np;
     t->host_p = (uint32_t *)malloc(np * sizeof(uint32_t));
@@ -300,14 +384,17 @@ int prime_table_create(PrimeTable *t, const Allocator &al, uint64_t y_max, cudaS
     t->l = (uint8_t *)dev_alloc(al, np);
     t->blk_r = (uint32_t *)dev_alloc(al, np * 4);
     t->blk_qm = (uint32_t *)dev_alloc(al, np * 4);
-    t->pattern = (uint32_t *)dev_alloc(al, kPatternPeriod * 4);
-    if (!t->p || !t->lg || !t->m || !t->l || !t->blk_r || !t->blk_qm || !t->pattern)
+    t->pat_even = (uint32_t *)dev_alloc(al, kPatternWords * 4);
+    t->pat_odd = (uint32_t *)dev_alloc(al, kPatternWords * 4);
+    if (!t->p || !t->lg || !t->m || !t->l || !t->blk_r || !t->blk_qm || !t->pat_even ||
+        !t->pat_odd)
         return 2;
     cudaMemcpyAsync(t->p, pr.data(), np * 4, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(t->lg, lg.data(), np * 4, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(t->m, mg.data(), np * 8, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(t->l, sh.data(), np, cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(t->pattern, pat.data(), kPatternPeriod * 4, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(t->pat_even, pe.data(), kPatternWords * 4, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(t->pat_odd, po.data(), kPatternWords * 4, cudaMemcpyHostToDevice, s);
     if (cudaStreamSynchronize(s) != cudaSuccess)
         return 3;
     return 0;
@@ -322,7 +409,8 @@ void prime_table_destroy(PrimeTable *t)
     dev_free(t->al, t->l, np);
     dev_free(t->al, t->blk_r, np * 4);
     dev_free(t->al, t->blk_qm, np * 4);
-    dev_free(t->al, t->pattern, kPatternPeriod * 4);
+    dev_free(t->al, t->pat_even, kPatternWords * 4);
+    dev_free(t->al, t->pat_odd, kPatternWords * 4);
     free(t->host_p);
     *t = PrimeTable();
 }
@@ -345,9 +433,7 @@ int sieve_block_enqueue(const PrimeTable *t, const SieveLaunch &L, cudaStream_t 
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(mu_sieve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kSieveTile * 4);
-        cudaFuncSetAttribute(m_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (kSieveTile + kSieveTile / 32) * 4);
+                             kSieveWords * 4);
         attr_set = true;
     }
     const uint64_t y2 = L.y1 + L.len - 1;
@@ -355,9 +441,9 @@ int sieve_block_enqueue(const PrimeTable *t, const SieveLaunch &L, cudaStream_t 
     if (P < 7)
         P = 7;
     const uint32_t np = prime_count_upto(t, P);
-    const uint32_t np_small = prime_count_upto(t, 1023);
+    const uint32_t np_small = prime_count_upto(t, 2047);
     int launches = 0;
-    const uint32_t tiles = (uint32_t)sieve_tiles(L.len);
+    const uint32_t tiles = (uint32_t)((L.len + kSieveTile - 1) / kSieveTile);
     if (np > 4) {
         sieve_block_prep_kernel<<<(np + 255) / 256, 256, 0, s>>>(L.y1, np, t->p, t->blk_r,
                                                                  t->blk_qm);
@@ -368,33 +454,45 @@ int sieve_block_enqueue(const PrimeTable *t, const SieveLaunch &L, cudaStream_t 
     a.len = L.len;
     a.np = np;
     a.np_small = np_small < np ? np_small : np;
-    a.thr_bias = (float)(8.0 * std::log2((double)P));
+    const uint32_t np_q = prime_count_upto(t, 127);
+    a.np_quarter = np_q < a.np_small ? np_q : a.np_small;
+    a.thr_bias = (float)(0.5 * kLogScale * std::log2((double)P));
     a.p = t->p;
     a.lg = t->lg;
     a.r = t->blk_r;
     a.qm = t->blk_qm;
-    a.pattern = t->pattern;
+    a.pat_even = t->pat_even;
+    a.pat_odd = t->pat_odd;
     a.m = t->m;
     a.l = t->l;
-    a.mu = L.mu;
-    a.mu_aux = L.mu_aux;
-    a.aux_end = L.aux_end;
-    a.tile_sum = L.tile_sum;
-    mu_sieve_kernel<<<tiles, kSieveThreads, kSieveTile * 4, s>>>(a);
+    a.Mloc = L.Mloc;
+    a.segsum = L.segsum;
+    a.mu_out = L.mu_out;
+    a.mu_base = L.mu_base;
+    a.mu_end = L.mu_end;
+    mu_sieve_kernel<<<tiles, kSieveThreads, kSieveWords * 4, s>>>(a);
     ++launches;
     if (L.mid)
         cudaEventRecord(L.mid, s);
     if (L.mid2)
         cudaEventRecord(L.mid2, s);
-    if (L.M) {
-        tile_carry_kernel<<<1, 1024, 0, s>>>(L.tile_sum, tiles, L.tile_off, L.carry);
-        m_scan_kernel<<<tiles, 1024, (kSieveTile + kSieveTile / 32) * 4, s>>>(
-            L.mu, L.len, L.tile_off, L.M, L.err);
-        launches += 2;
-    }
+    const uint32_t nseg = (uint32_t)sieve_segments(L.len);
+    seg_carry_kernel<<<(nseg + 1023) / 1024, 1024, 0, s>>>(L.segsum, nseg, L.carry_in, L.segoff,
+                                                          L.carry_out);
+    ++launches;
     if (cudaGetLastError() != cudaSuccess)
         return -1;
     return launches;
+}
+
+int expand_M_enqueue(const int16_t *Mloc, const int64_t *segoff, uint64_t len, int32_t *M,
+                     uint32_t *err, cudaStream_t s)
+{
+    uint64_t blocks = (len + 255) / 256;
+    if (blocks > 152 * 32)
+        blocks = 152 * 32;
+    expand_M_kernel<<<(unsigned)blocks, 256, 0, s>>>(Mloc, segoff, len, M, err);
+    return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
 // ---------------------------------------------------------------------------

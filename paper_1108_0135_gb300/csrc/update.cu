@@ -206,10 +206,22 @@ __global__ void __launch_bounds__(kDenseThreads) dense_update_kernel(DenseArgs a
 // ---------------------------------------------------------------------------
 // Gathered terms of one sieve block [y1, y2].
 // ---------------------------------------------------------------------------
-// Per entry: the j-range of the block, j in [max(jlo, floor(k/(y2+1))+1),
-// min(jcur, floor(k/y1))] (so floor(k/j) lies in the block), its number of
-// warp items, and the cursor for the next block.  Also adds the boundary
-// term -M(yc) floor(k/(yc+1)) of the dense form when yc is in this block.
+// Entries with at most this many gathered terms in a tile or block are
+// handled by one lane; more, by a whole warp.
+constexpr uint64_t kLaneTerms = 48;
+
+// M(y) of the current block from its segment offsets and int16 values.
+__device__ __forceinline__ int64_t block_M(const int64_t *segoff, const int16_t *Mloc,
+                                           uint64_t i)
+{
+    return segoff[i >> kSegShift] + (int64_t)Mloc[i];
+}
+
+// Per entry: the j-range of the global-memory part [y_lo, y2] of the block,
+// j in [max(jlo, floor(k/(y2+1))+1), min(jcur, floor(k/y_lo))] (so
+// floor(k/j) lies in it), its number of warp items, and the cursor for the
+// next block.  Also adds the boundary term -M(yc) floor(k/(yc+1)) of the
+// dense form when yc is in this block.
 __global__ void sparse_prep_kernel(SparseBlockArgs b, SparseArgs a)
 {
     const uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -217,21 +229,34 @@ __global__ void sparse_prep_kernel(SparseBlockArgs b, SparseArgs a)
         return;
     const uint64_t k2 = a.K[e] << 1;
     const uint64_t jc = a.JCUR[e], jlo = a.JLO[e];
-    const uint64_t q1 = div_magic(k2, b.m_y1, b.l_y1);      // floor(k / y1)
+    const uint64_t q1 = div_magic(k2, a.m_ylo, a.l_ylo);    // floor(k / y_lo)
     const uint64_t q2 = div_magic(k2, b.m_y2p1, b.l_y2p1);  // floor(k / (y2+1))
     const uint64_t jtop = jc < q1 ? jc : q1;
     const uint64_t jbot = (q2 + 1) > jlo ? (q2 + 1) : jlo;
     const uint64_t cnt = jtop >= jbot ? jtop - jbot + 1 : 0;
     a.JTOP[e] = jtop;
     a.JBOT[e] = jbot;
-    a.ICNT[e] = (uint32_t)((cnt + kSparseItem - 1) / kSparseItem);
     a.JCUR[e] = jc < q2 ? jc : q2;
+    uint64_t add = 0;
+    if (cnt <= kLaneTerms) {
+        // few terms: done here, by this thread
+        int64_t acc = 0;
+        for (uint64_t j = jbot; j <= jtop && cnt; ++j) {
+            const uint64_t y = div_magic(k2, a.MG[j], magic_shift(j));
+            acc += block_M(a.segoff, a.Mloc, y - b.y1);
+        }
+        add = (uint64_t)acc;
+        a.ICNT[e] = 0;
+    } else {
+        a.ICNT[e] = (uint32_t)((cnt + kSparseItem - 1) / kSparseItem);
+    }
     const uint64_t yc = a.YCE[e];
     if (yc >= b.y1 && yc <= b.y2) {
-        const int64_t Myc = a.Mblk[yc - b.y1];
-        atomicAdd(reinterpret_cast<unsigned long long *>(a.S + e),
-                  (unsigned long long)(-(int64_t)((uint64_t)Myc * a.JC0[e])));
+        const int64_t Myc = block_M(a.segoff, a.Mloc, yc - b.y1);
+        add -= (uint64_t)Myc * a.JC0[e];
     }
+    if (add)
+        atomicAdd(reinterpret_cast<unsigned long long *>(a.S + e), (unsigned long long)add);
 }
 
 // One warp per item of kSparseItem consecutive j of one entry, lanes over j:
@@ -259,11 +284,93 @@ __global__ void __launch_bounds__(256) sparse_update_kernel(SparseBlockArgs b, S
         int64_t acc = 0;
         for (uint64_t j = jt - lane; j >= jb && j <= jt; j -= 32) {
             const uint64_t y = div_magic(k2, a.MG[j], magic_shift(j));
-            acc += a.Mblk[y - b.y1];
+            acc += block_M(a.segoff, a.Mloc, y - b.y1);
         }
         acc = warp_sum_i64(acc);
         if (lane == 0)
             atomicAdd(reinterpret_cast<unsigned long long *>(a.S + e), (unsigned long long)acc);
+    }
+}
+
+// Shared-memory gather path for the low, dense part of a block.  A work item
+// is one tile [t1, t1+len) of y and a range of entries of one target.  The
+// tile's M(y) - M(t1-1) is staged in shared memory as int16 (|value| <= 3/4
+// of the tile); every entry with gathered terms in the tile -- j in
+// [max(jlo, floor(k/(t1+len))+1), min(jcur, floor(k/t1))] -- adds
+// sum_j M(floor(k/j)) = sum_j (staged value) + count * M(t1-1).  Warps take
+// 32 entries at a time (lane per entry for the range), then each entry with
+// terms in turn, lanes over its j.
+__global__ void __launch_bounds__(512) gather_tile_kernel(GatherArgs a)
+{
+    extern __shared__ int16_t Mt[];  // kGatherTile
+    __shared__ uint32_t s_item;
+    __shared__ int64_t s_base;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    uint32_t staged = 0xffffffffu;
+    for (;;) {
+        if (threadIdx.x == 0)
+            s_item = atomicAdd(a.counter, 1u);
+        __syncthreads();
+        const uint32_t it = s_item;
+        if (it >= a.nitems)
+            break;
+        const GatherItem I = a.items[it];
+        const GatherTile T = a.tiles[I.tile];
+        if (I.tile != staged) {
+            const uint64_t o1 = T.t1 - a.y1;
+            const int64_t base = (o1 == 0) ? a.segoff[0] : block_M(a.segoff, a.Mloc, o1 - 1);
+            for (uint32_t i = threadIdx.x; i < T.len; i += blockDim.x)
+                Mt[i] = (int16_t)(block_M(a.segoff, a.Mloc, o1 + i) - base);
+            if (threadIdx.x == 0)
+                s_base = base;
+            staged = I.tile;
+        }
+        __syncthreads();
+        const int64_t base = s_base;
+        for (uint32_t eb = I.e0 + (uint32_t)warp * 32u; eb < I.e1; eb += (uint32_t)nwarp * 32u) {
+            const uint32_t e = eb + (uint32_t)lane;
+            uint64_t k2 = 0, jt = 0, jb = 1;
+            if (e < I.e1) {
+                k2 = a.K[e] << 1;
+                const uint64_t jc = a.JCUR[e], jlo = a.JLO[e];
+                const uint64_t q1 = div_magic(k2, T.m1, T.l1);  // floor(k / t1)
+                const uint64_t q2 = div_magic(k2, T.m2, T.l2);  // floor(k / (t1+len))
+                jt = jc < q1 ? jc : q1;
+                jb = (q2 + 1) > jlo ? (q2 + 1) : jlo;
+            }
+            const uint64_t cnt = jt >= jb ? jt - jb + 1 : 0;
+            // entries with few terms: one lane each, serially
+            if (cnt > 0 && cnt <= kLaneTerms) {
+                int acc = 0;
+                for (uint64_t j = jb; j <= jt; ++j) {
+                    const uint64_t y = div_magic(k2, a.MG[j], magic_shift(j));
+                    acc += Mt[y - T.t1];
+                }
+                const int64_t tot = (int64_t)acc + (int64_t)cnt * base;
+                atomicAdd(reinterpret_cast<unsigned long long *>(a.S + e), (unsigned long long)tot);
+            }
+            // entries with many terms: the whole warp, lanes over j
+            uint32_t mask = __ballot_sync(0xffffffffu, cnt > kLaneTerms);
+            while (mask) {
+                const int src = __ffs(mask) - 1;
+                mask &= mask - 1;
+                const uint64_t jts = __shfl_sync(0xffffffffu, jt, src);
+                const uint64_t jbs = __shfl_sync(0xffffffffu, jb, src);
+                const uint64_t k2s = __shfl_sync(0xffffffffu, k2, src);
+                int acc = 0;
+                for (uint64_t j = jts - lane; j >= jbs && j <= jts; j -= 32) {
+                    const uint64_t y = div_magic(k2s, a.MG[j], magic_shift(j));
+                    acc += Mt[y - T.t1];
+                }
+                int64_t tot = warp_sum_i64((int64_t)acc);
+                if (lane == 0) {
+                    tot += (int64_t)(jts - jbs + 1) * base;
+                    atomicAdd(reinterpret_cast<unsigned long long *>(a.S + eb + src),
+                              (unsigned long long)tot);
+                }
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -376,6 +483,30 @@ int sparse_block_enqueue(const SparseBlockArgs &b, const SparseArgs &a, uint32_t
     sparse_update_kernel<<<sms * 8, 256, 0, s>>>(b, a);
     ++launches;
     return cudaGetLastError() == cudaSuccess ? launches : -1;
+}
+
+int gather_tiles_enqueue(const GatherArgs &a, cudaStream_t s)
+{
+    static bool attr = false;
+    const int smem = kGatherTile * 2;
+    if (!attr) {
+        cudaFuncSetAttribute(gather_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        attr = true;
+    }
+    if (a.nitems == 0)
+        return 0;
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, gather_tile_kernel, 512, smem);
+    if (per < 1)
+        per = 1;
+    uint32_t grid = (uint32_t)(sms * per);
+    if (grid > a.nitems)
+        grid = a.nitems;
+    cudaMemsetAsync(a.counter, 0, 4, s);
+    gather_tile_kernel<<<grid, 512, smem, s>>>(a);
+    return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
 int resolve_enqueue(const QueryDev *qs, uint32_t nq, const uint64_t *S, const uint64_t *K,

@@ -49,17 +49,49 @@ struct SparseBlockArgs {
     uint32_t l_y1, l_y2p1;
 };
 
+// M(y) of the current block: segoff[(y - y1) >> kSegShift] + Mloc[y - y1].
 struct SparseArgs {
     uint64_t nent;
+    uint64_t y_lo;  // first y of the block handled by the global-memory path
+    uint64_t m_ylo;
+    uint32_t l_ylo;
     const uint64_t *K, *JLO, *JC0, *YCE, *MG;
     uint64_t *JCUR, *JTOP, *JBOT, *S;
     uint32_t *ICNT, *IOFF;
-    const int32_t *Mblk;
+    const int16_t *Mloc;
+    const int64_t *segoff;
 };
 
 struct QueryDev {
     uint64_t X;    // entries of the target
     uint64_t off;  // global index of its entry x = 1
+};
+
+// Shared-memory gather path: one tile of kGatherTile y (or fewer) and the
+// division constants of its first y and of its last y + 1.
+struct GatherTile {
+    uint64_t t1;
+    uint64_t m1, m2;
+    uint32_t len;
+    uint32_t l1, l2;
+    uint32_t pad;
+};
+
+// Work item: entries [e0, e1) (global indices, one target) for one tile.
+struct GatherItem {
+    uint32_t tile, e0, e1, pad;
+};
+
+struct GatherArgs {
+    uint64_t y1;  // block start (index base of Mloc / segoff)
+    const GatherTile *tiles;
+    const GatherItem *items;
+    uint32_t nitems;
+    uint32_t *counter;
+    const int16_t *Mloc;
+    const int64_t *segoff;
+    const uint64_t *K, *JLO, *JCUR, *MG;
+    uint64_t *S;
 };
 
 int magic_table_enqueue(uint64_t *MG, uint64_t nd, cudaStream_t s);
@@ -68,6 +100,7 @@ int dense_list_enqueue(const int8_t *mu_aux, uint64_t ydense, const uint64_t *MG
 int dense_update_enqueue(const DenseArgs &a, cudaStream_t s);
 int sparse_block_enqueue(const SparseBlockArgs &b, const SparseArgs &a, uint32_t *scan_scratch,
                          cudaStream_t s);
+int gather_tiles_enqueue(const GatherArgs &a, cudaStream_t s);
 int resolve_enqueue(const QueryDev *qs, uint32_t nq, const uint64_t *S, const uint64_t *K,
                     uint64_t *R, cudaStream_t s);
 
