@@ -290,11 +290,12 @@ def run_native(args, world, rank, local):
 
     # roofline of the dominant kernel class
     peaks, peak_src = load_peaks()
-    phases = {"mu_sieve": stats["sieve_ms"], "m_scan": stats["scan_ms"],
+    phases = {"mu_sieve": stats["sieve_ms"], "seg_carry": stats["scan_ms"],
               "update_dense": stats["dense_ms"], "update_gathered": stats["gather_ms"],
               "resolve": stats["resolve_ms"]}
-    dom = max(phases, key=phases.get)
-    roof = roofline_for(dom, phases[dom], info, cfg, stats, peaks, peak_src)
+    roofs = rooflines(phases, stats, peaks, int(stats["blocks"]))
+    dom = max(roofs, key=lambda k: phases[k])
+    roof = roofs[dom]
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -323,37 +324,58 @@ def run_native(args, world, rank, local):
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms_max},
             "gpu_launches": int(stats["kernels"]) * args.steps,
             "roofline": roof,
+            "rooflines": roofs,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
 
 
-def roofline_for(kernel, ms, info, cfg, stats, peaks, src):
-    """Roofline record of the dominant kernel class, per launch-average of
-    the timed region.  See the design doc for the per-unit figures."""
-    if ms <= 0:
-        return None
+# DRAM bytes (read + write) per launch from one ncu capture of the current
+# kernel (profiles/), or None when the kernel changed since the capture.
+TRAFFIC_PER_LAUNCH = {
+    "mu_sieve": 0.345e6 + 476.590e6,       # profiles/mu_sieve_1e16.md (one 2^28-y block)
+    "update_dense": 989.370e6 + 5.861e6,   # profiles/dense_update_1e16.md
+    "update_gathered": 1670.806e6 + 56.108e6,  # profiles/gather_tile_1e16.md (first block)
+}
+
+SIX_OVER_PI2 = 6.0 / math.pi ** 2
+
+
+def rooflines(phases, stats, peaks, nblocks):
+    """Roofline records per kernel class of the timed region.
+
+    All classes here are bound by 32-bit integer issue (no tensor cores, no
+    floating point; HBM traffic is 2 B per sieved y).  The peak is derived
+    from unit counts and the clock: 152 SMs x 64 integer lanes per SM per
+    clock (the IMAD and ALU pipes each retire 64 lanes/clock/SM on GB300,
+    which an integer probe reproduced: 68 and 65) x the maximum SM clock.
+    Algorithmic integer operations per unit:
+      mu_sieve (fused a1+a2): one per sieve update (y, p | y or p^2 | y for
+        every sieving prime p) plus two per y (decision + scan add);
+      update_dense: four 32-bit multiplies per squarefree term (the
+        64x64->128 multiply-high of the quotient), squarefree terms =
+        (6/pi^2) x dense y-range;
+      update_gathered: four per gathered term (same multiply-high)."""
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    if kernel in ("update_dense", "update_gathered", "mu_sieve"):
-        # integer-pipe bound: 64-bit multiply-high equivalents per second
-        # against 152 SMs x 64 IMAD lanes/clk / 4 IMAD per mulhi64 x clock
-        peak = 152 * 64 / 4 * sm_mhz * 1e6 / 1e12
-        if kernel == "update_dense":
-            units = 0.6079 * info["direct_terms"] * 1.6  # squarefree y of the dense range
-        elif kernel == "update_gathered":
-            units = info["gathered_terms"] * (1 - 1 / 1.6)
-        else:
-            units = stats["y_sieved"] * 1.0
-        achieved = units / (ms / 1e3) / 1e12
-        return {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak,
-                "unit": "T mulhi64/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": f"derived: 152 SM x 64 IMAD/clk / 4 x {sm_mhz:.0f} MHz"}
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    bytes_ = stats["y_sieved"] * 5.0
-    achieved = bytes_ / (ms / 1e3) / 1e9
-    return {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": hbm,
-            "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
-            "peak_source": f"{src} copy bandwidth"}
+    peak = 152 * 64 * sm_mhz * 1e6 / 1e12  # T int-op/s
+    ops = {
+        "mu_sieve": stats["sieve_updates"] + 2.0 * stats["y_sieved"],
+        "update_dense": 4.0 * SIX_OVER_PI2 * stats["dense_y"],
+        "update_gathered": 4.0 * stats["gather_j"],
+    }
+    launches = {"mu_sieve": nblocks, "update_dense": 1, "update_gathered": nblocks}
+    out = {}
+    for k, v in ops.items():
+        ms = phases.get(k, 0.0)
+        if ms <= 0:
+            continue
+        achieved = v / (ms / 1e3) / 1e12
+        out[k] = {"bound": "alu", "kernel": k, "achieved": achieved, "peak": peak,
+                  "unit": "T int-op/s", "frac": achieved / peak,
+                  "traffic": TRAFFIC_PER_LAUNCH.get(k),
+                  "launches_per_step": launches[k],
+                  "peak_source": f"derived: 152 SM x 64 int lanes/clk x {sm_mhz:.0f} MHz"}
+    return out
 
 
 def main():

@@ -162,6 +162,12 @@ typedef struct {
     uint64_t y_sieved;    /* y values sieved                                */
     uint64_t terms;       /* direct + gathered update terms, all targets    */
     uint64_t kernels;     /* kernel launches of the last run                */
+    uint64_t dense_y;     /* y values covered by the dense (mu-form) part,
+                             summed over entries                            */
+    uint64_t gather_j;    /* gathered terms (one per j), all entries        */
+    double sieve_updates; /* sieve updates: sum over blocks of the block
+                             length times sum_{p <= sqrt(block end)}
+                             (1/p + 1/p^2)                                  */
     uint64_t h2d_bytes;   /* host-to-device bytes of the plan's inputs      */
     uint64_t d2h_bytes;   /* device-to-host bytes read by mertens_result
                              since the last mertens_run                     */

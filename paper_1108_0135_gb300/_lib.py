@@ -41,6 +41,8 @@ class mertens_run_stats(ctypes.Structure):
                 ("resolve_ms", ctypes.c_double), ("runs", ctypes.c_uint64),
                 ("blocks", ctypes.c_uint64), ("y_sieved", ctypes.c_uint64),
                 ("terms", ctypes.c_uint64), ("kernels", ctypes.c_uint64),
+                ("dense_y", ctypes.c_uint64), ("gather_j", ctypes.c_uint64),
+                ("sieve_updates", ctypes.c_double),
                 ("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64)]
 
 

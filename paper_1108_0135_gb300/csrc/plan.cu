@@ -104,7 +104,8 @@ struct mertens_plan_s {
     std::vector<uint64_t> direct, gathered, ymax_q;
     uint64_t nent = 0;
     uint64_t y_max = 0, block_len = 0, nblocks = 0, ydense = 0, jmax = 0, mg_n = 0;
-    uint64_t terms = 0;
+    uint64_t terms = 0, dense_y = 0, gather_j = 0;
+    double sieve_updates = 0;
     // device buffers
     PrimeTable pt;
     uint64_t *dK = nullptr, *dJLO = nullptr, *dJC0 = nullptr, *dJCUR = nullptr, *dYCE = nullptr;
@@ -365,6 +366,9 @@ int mertens_plan(mertens_plan_t *out, const mertens_u128 *n, size_t count, merte
                 ymq = std::max(ymq, need);
                 p->ydense = std::max(p->ydense, yc);
                 p->jmax = std::max(p->jmax, jc0);
+                p->dense_y += yc;
+                if (jc0 >= JLO[e])
+                    p->gather_j += jc0 - JLO[e] + 1;
             }
         }
         p->direct.push_back(d);
@@ -548,6 +552,21 @@ int mertens_plan(mertens_plan_t *out, const mertens_u128 *n, size_t count, merte
         int prc = prime_table_create(&p->pt, p->al, p->y_max, nullptr);
         if (prc != 0)
             rc = prc == 6 ? MERTENS_ENOTSUP : (prc == 2 ? MERTENS_ENOMEM : MERTENS_ECUDA);
+    }
+    if (rc == MERTENS_OK) {
+        // algorithmic sieve updates: each block of length len sieved with the
+        // primes p <= max(7, sqrt(block end)) costs len * sum (1/p + 1/p^2)
+        std::vector<double> pre(p->pt.np + 1, 0.0);
+        for (uint32_t i = 0; i < p->pt.np; ++i) {
+            const double q = (double)p->pt.host_p[i];
+            pre[i + 1] = pre[i] + 1.0 / q + 1.0 / (q * q);
+        }
+        for (uint64_t b = 0; b < p->nblocks; ++b) {
+            const uint64_t y1 = 1 + b * block_len;
+            const uint64_t y2 = std::min(y1 + block_len - 1, p->y_max);
+            const uint64_t P = std::max<uint64_t>(7, isqrt64(y2));
+            p->sieve_updates += (double)(y2 - y1 + 1) * pre[prime_count_upto(&p->pt, P)];
+        }
     }
     if (rc == MERTENS_OK) {
         std::vector<QueryDev> qs(count);
@@ -867,6 +886,9 @@ int mertens_run_stats_get(mertens_plan_t p, mertens_run_stats *st)
     st->y_sieved = p->y_max;
     st->terms = p->terms;
     st->kernels = p->kernels;
+    st->dense_y = p->dense_y;
+    st->gather_j = p->gather_j;
+    st->sieve_updates = p->sieve_updates;
     st->h2d_bytes = p->h2d_bytes;
     st->d2h_bytes = p->d2h_bytes;
     st->runs = p->prof_runs;

@@ -338,13 +338,18 @@ __global__ void __launch_bounds__(512) gather_tile_kernel(GatherArgs a)
                 jt = jc < q1 ? jc : q1;
                 jb = (q2 + 1) > jlo ? (q2 + 1) : jlo;
             }
-            const uint64_t cnt = jt >= jb ? jt - jb + 1 : 0;
+            // j < 2^32 (j <= sqrt(k) < 2^32) and y - t1 < 2^15: 32-bit loop
+            // counters and offsets
+            const uint32_t cnt = jt >= jb ? (uint32_t)(jt - jb + 1) : 0u;
+            const uint32_t t1lo = (uint32_t)T.t1;
             // entries with few terms: one lane each, serially
             if (cnt > 0 && cnt <= kLaneTerms) {
                 int acc = 0;
-                for (uint64_t j = jb; j <= jt; ++j) {
-                    const uint64_t y = div_magic(k2, a.MG[j], magic_shift(j));
-                    acc += Mt[y - T.t1];
+                const uint32_t j0 = (uint32_t)jb;
+                for (uint32_t i = 0; i < cnt; ++i) {
+                    const uint32_t j = j0 + i;
+                    const uint64_t y = div_magic(k2, a.MG[j], 32u - __clz(j - 1u));
+                    acc += Mt[(uint32_t)y - t1lo];
                 }
                 const int64_t tot = (int64_t)acc + (int64_t)cnt * base;
                 atomicAdd(reinterpret_cast<unsigned long long *>(a.S + e), (unsigned long long)tot);
@@ -354,17 +359,18 @@ __global__ void __launch_bounds__(512) gather_tile_kernel(GatherArgs a)
             while (mask) {
                 const int src = __ffs(mask) - 1;
                 mask &= mask - 1;
-                const uint64_t jts = __shfl_sync(0xffffffffu, jt, src);
-                const uint64_t jbs = __shfl_sync(0xffffffffu, jb, src);
+                const uint32_t jts = (uint32_t)__shfl_sync(0xffffffffu, jt, src);
+                const uint32_t cns = __shfl_sync(0xffffffffu, cnt, src);
                 const uint64_t k2s = __shfl_sync(0xffffffffu, k2, src);
                 int acc = 0;
-                for (uint64_t j = jts - lane; j >= jbs && j <= jts; j -= 32) {
-                    const uint64_t y = div_magic(k2s, a.MG[j], magic_shift(j));
-                    acc += Mt[y - T.t1];
+                for (uint32_t i = (uint32_t)lane; i < cns; i += 32u) {
+                    const uint32_t j = jts - i;
+                    const uint64_t y = div_magic(k2s, a.MG[j], 32u - __clz(j - 1u));
+                    acc += Mt[(uint32_t)y - t1lo];
                 }
                 int64_t tot = warp_sum_i64((int64_t)acc);
                 if (lane == 0) {
-                    tot += (int64_t)(jts - jbs + 1) * base;
+                    tot += (int64_t)cns * base;
                     atomicAdd(reinterpret_cast<unsigned long long *>(a.S + eb + src),
                               (unsigned long long)tot);
                 }
@@ -377,21 +383,38 @@ __global__ void __launch_bounds__(512) gather_tile_kernel(GatherArgs a)
 // ---------------------------------------------------------------------------
 // Resolve (Sec. 2): for x = X down to 1,
 //   M[x] = 1 - S[x] - sum_{j=2}^{floor(X/x)} M[x j]   (mod 2^64),
-// level by level: all x with the same q = floor(X/x) only read entries of
-// smaller q.  One CTA per target.
+// in three phases, one CTA per target, r = min(floor(sqrt(X)), kResolveSmall):
+//  A. x > r level by level: all x with the same q = floor(X/x) only read
+//     entries of smaller q (parallel over the x of a level);
+//  B. for x <= r, the part of the sum with x j > r (all known after A),
+//     parallel over x;
+//  C. x = r down to 1, the remaining sum over x j <= r from shared memory.
 // ---------------------------------------------------------------------------
+constexpr int kResolveSmall = 4096;
+
 __global__ void __launch_bounds__(1024) resolve_kernel(const QueryDev *__restrict__ qs,
                                                        const uint64_t *__restrict__ S,
                                                        const uint64_t *__restrict__ K,
                                                        uint64_t *__restrict__ R)
 {
+    __shared__ uint64_t Tsm[kResolveSmall + 1];  // phase B sums, then phase C values
     const QueryDev Q = qs[blockIdx.x];
     const uint64_t X = Q.X, base = Q.off;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    uint64_t r = (uint64_t)sqrt((double)X);
+    while (r * r > X)
+        --r;
+    while ((r + 1) * (r + 1) <= X)
+        ++r;
+    if (r > (uint64_t)kResolveSmall)
+        r = kResolveSmall;
+    // A
     uint64_t xhi = X;
-    while (xhi >= 1) {
+    while (xhi > r) {
         const uint64_t qv = X / xhi;
-        const uint64_t xlo = X / (qv + 1) + 1;
+        uint64_t xlo = X / (qv + 1) + 1;
+        if (xlo <= r)
+            xlo = r + 1;
         const uint64_t size = xhi - xlo + 1;
         if (size >= blockDim.x || qv <= 8) {
             for (uint64_t x = xlo + threadIdx.x; x <= xhi; x += blockDim.x) {
@@ -415,6 +438,42 @@ __global__ void __launch_bounds__(1024) resolve_kernel(const QueryDev *__restric
         }
         __syncthreads();
         xhi = xlo - 1;
+    }
+    // B: Tsm[x] = 1 - S[x] - sum_{j >= 2, x j > r} M[x j]
+    for (uint64_t x = 1 + warp; x <= r; x += nwarp) {
+        const uint64_t jmax = X / x;
+        uint64_t j0 = r / x + 1;
+        if (j0 < 2)
+            j0 = 2;
+        uint64_t acc = 0;
+        for (uint64_t j = j0 + lane; j <= jmax; j += 32)
+            acc += R[base + x * j - 1];
+        acc = warp_sum_u64(acc);
+        if (lane == 0) {
+            const uint64_t e = base + x - 1;
+            Tsm[x] = (K[e] == 1) ? 1ull : 1ull - S[e] - acc;
+        }
+    }
+    __syncthreads();
+    // C: the rest, x j <= r, in decreasing x (one warp, values in Tsm)
+    if (warp == 0) {
+        for (uint64_t x = r; x >= 1; --x) {
+            const uint64_t e = base + x - 1;
+            uint64_t acc = 0;
+            if (K[e] != 1) {
+                const uint64_t jmax = r / x;
+                for (uint64_t j = 2 + lane; j <= jmax; j += 32)
+                    acc += Tsm[x * j];
+                acc = warp_sum_u64(acc);
+            }
+            const uint64_t v = Tsm[x] - acc;
+            __syncwarp();
+            if (lane == 0) {
+                Tsm[x] = v;
+                R[e] = v;
+            }
+            __syncwarp();
+        }
     }
 }
 
