@@ -201,6 +201,34 @@ int mertens_sieve_mu(uint64_t y1, uint64_t len, int8_t *mu_dev, void *stream);
 int mertens_sieve_M(uint64_t y1, uint64_t len, int64_t carry, int32_t *M_dev,
                     void *stream);
 
+/*
+ * mertens_sieve_M_noalloc -- the same result as mertens_sieve_M (M(y) for
+ * y = y1 .. y1+len-1 into M_dev as int32, given carry = M(y1-1)), for callers
+ * that cannot allocate device memory: for example code that runs inside a
+ * framework which has reserved the device memory for its own pool, or a
+ * latency-critical loop that cannot afford the device-wide synchronisation
+ * and the possible failure of cudaMalloc/cudaFree.  The paper has no
+ * counterpart; this is a property of the library, not of the method.
+ *
+ * All scratch (prime table, pre-sieve pattern, int16 partial sums, segment
+ * offsets, carry and status words; about 6.2 MB) lives in one fixed device
+ * array inside the library, held on every GPU that loads the library until
+ * the process exits.  Limits: 1 <= len <= 2^21 and y1 + len - 1 < 2^40,
+ * otherwise MERTENS_EINVAL with an explanatory mertens_last_error().
+ * The call allocates no device memory and no host heap memory.
+ *
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture on the
+ * device.  Every call uses the same array and leaves its contents behind, so
+ * calls that overlap on the GPU race: serialise them (one stream, or wait for
+ * one call before starting another).  The call synchronises `stream`.
+ * M_dev: device, 4-byte aligned, len int32, owned by the caller.
+ * Errors: MERTENS_EINVAL, MERTENS_EOVERFLOW (some |M(y)| >= 2^31),
+ * MERTENS_ECUDA.
+ */
+int mertens_sieve_M_noalloc(uint64_t y1, uint64_t len, int64_t carry, int32_t *M_dev,
+                            void *stream);
+
 #ifdef __cplusplus
 }
 #endif

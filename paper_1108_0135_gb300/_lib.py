@@ -55,7 +55,7 @@ EXPORTS = [
     "mertens_strerror", "mertens_last_error", "mertens_set_allocator", "mertens_plan",
     "mertens_run", "mertens_result", "mertens_destroy", "mertens_describe",
     "mertens_plan_info", "mertens_plan_set_profiling", "mertens_run_stats_get",
-    "mertens_sieve_mu", "mertens_sieve_M",
+    "mertens_sieve_mu", "mertens_sieve_M", "mertens_sieve_M_noalloc",
 ]
 
 _lock = threading.Lock()
@@ -107,6 +107,8 @@ def load():
         lib.mertens_sieve_mu.restype = c_int
         lib.mertens_sieve_M.argtypes = [u64, u64, i64, P, P]
         lib.mertens_sieve_M.restype = c_int
+        lib.mertens_sieve_M_noalloc.argtypes = [u64, u64, i64, P, P]
+        lib.mertens_sieve_M_noalloc.restype = c_int
         _lib = lib
         return lib
 
@@ -239,6 +241,13 @@ def mertens_sieve_mu(y1: int, length: int, mu_dev, stream=None) -> None:
 def mertens_sieve_M(y1: int, length: int, carry: int, M_dev, stream=None) -> None:
     _check(load().mertens_sieve_M(int(y1), int(length), int(carry), _ptr(M_dev),
                                   _stream(stream)), "mertens_sieve_M")
+
+
+def mertens_sieve_M_noalloc(y1: int, length: int, carry: int, M_dev, stream=None) -> None:
+    """mertens_sieve_M without any device allocation (fixed library scratch;
+    len <= 2^21, y1 + len - 1 < 2^40; overlapping calls race)."""
+    _check(load().mertens_sieve_M_noalloc(int(y1), int(length), int(carry), _ptr(M_dev),
+                                          _stream(stream)), "mertens_sieve_M_noalloc")
 
 
 _alloc_keepalive = []
