@@ -46,6 +46,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true",
                     help="skip the timed oracle sample (cpu_baseline key)")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the one-shot M(10^18) wall-time measurement")
     return ap.parse_args()
 
 
@@ -243,9 +245,8 @@ def run_native(args, world, rank, local):
     if cfg["pin"] is not None and m_n != cfg["pin"]:
         raise SystemExit(f"wrong result: M({n_list[0]}) = {m_n}, expected {cfg['pin']}")
 
-    # timed region: K steps, CUDA events on the launching stream, phase
-    # events of the library recorded on the same stream
-    pm.mertens_plan_set_profiling(plan, True)
+    # timed region: K steps (whole runs replayed from the plan's CUDA graph),
+    # CUDA events on the launching stream, clocks sampled meanwhile
     clocks = ClockSampler(local)
     barrier(world)
     torch.cuda.synchronize()
@@ -260,12 +261,47 @@ def run_native(args, world, rank, local):
     barrier(world)
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1) / args.steps
+    m_chk, _ = pm.mertens_result(plan, 0)
+    assert m_chk == m_n
+    # the same K steps launched kernel by kernel with the library's phase
+    # events on the same stream: per-kernel-class times for the rooflines
+    pm.mertens_plan_set_profiling(plan, True)
+    torch.cuda.synchronize()
+    pe0 = torch.cuda.Event(enable_timing=True)
+    pe1 = torch.cuda.Event(enable_timing=True)
+    pe0.record(stream)
+    for _ in range(args.steps):
+        pm.mertens_run(plan, stream)
+    pe1.record(stream)
+    torch.cuda.synchronize()
+    ms_eager = pe0.elapsed_time(pe1) / args.steps
     stats = pm.mertens_run_stats_get(plan)
     m_chk, _ = pm.mertens_result(plan, 0)
     assert m_chk == m_n
     pm.mertens_destroy(plan)
     ms_max = max_over_ranks(ms, world)
     value = terms * world / (ms_max / 1e3)
+
+    # M(10^18) wall time (the metric's second figure), one warm run timed
+    extra = {}
+    if world == 1 and args.config == "1e16" and not args.no_extra:
+        p18 = pm.mertens_plan([10**18])
+        i18 = pm.mertens_plan_info(p18, 0)
+        pm.mertens_run(p18, stream)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pm.mertens_run(p18, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        m18, _ = pm.mertens_result(p18, 0)
+        pm.mertens_destroy(p18)
+        t18 = e0.elapsed_time(e1) / 1e3
+        extra["M_1e18"] = {"M": m18, "expected_table1": -46758740, "wall_time_s": t18,
+                           "u": i18["u"], "X": i18["X"],
+                           "update_terms_per_s": (i18["direct_terms"] + i18["gathered_terms"])
+                           / t18}
 
     # e2e: the user call with host inputs and host results, every step
     host_out = torch.empty(info["X"], dtype=torch.int64, pin_memory=True)
@@ -325,6 +361,10 @@ def run_native(args, world, rank, local):
             "gpu_launches": int(stats["kernels"]) * args.steps,
             "roofline": roof,
             "rooflines": roofs,
+            "phase_timing": f"library CUDA events on the launching stream, {args.steps} steps "
+                            f"launched kernel by kernel right after the timed graph-replay "
+                            f"steps ({ms_eager:.2f} ms/step that way)",
+            "extra": extra,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

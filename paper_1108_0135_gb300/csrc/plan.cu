@@ -139,6 +139,10 @@ struct mertens_plan_s {
     uint64_t prof_runs = 0;
     uint64_t kernels = 0;
     uint64_t h2d_bytes = 0, d2h_bytes = 0;
+    // captured whole run (replayed by later runs)
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    uint64_t graph_kernels = 0;
 
     template <typename T>
     T *alloc(size_t count)
@@ -383,9 +387,12 @@ int mertens_plan(mertens_plan_t *out, const mertens_u128 *n, size_t count, merte
         delete p;
         return MERTENS_ENOTSUP;
     }
-    if (block_len == 0)
+    if (block_len == 0) {
+        // one block when it fits 2^28 y, else 2^28 (up to 2^36 y) or 2^30 y blocks
+        const uint64_t cap = p->y_max > (1ull << 36) ? (1ull << 30) : (1ull << 28);
         block_len = std::min<uint64_t>(((p->y_max + kSieveTile - 1) / kSieveTile) * kSieveTile,
-                                       1ull << 28);
+                                       cap);
+    }
     if (block_len > (1ull << 31)) {
         set_last_error("mertens_plan: block_len must be <= 2^31");
         delete p;
@@ -442,12 +449,25 @@ int mertens_plan(mertens_plan_t *out, const mertens_u128 *n, size_t count, merte
     }
     const double kItemWork = 2.0e5;
     {
+        // Gathered terms per y near y are about (n / y^2) ln X summed over
+        // the targets; shared-memory tiles pay while that is at least ~2,
+        // i.e. up to y ~ sqrt(sum n ln X / 2) (2.5e8 for n = 1e16, X = 2.5e5).
+        // A tile pays while its terms (32768 (sum n ln X) / y^2) are at least
+        // a quarter of the entries it must check (all of them, E).
+        double acc = 0;
+        for (size_t i = 0; i < count; ++i)
+            acc += (double)p->n[i] * std::log((double)std::max<uint64_t>(p->X[i], 2));
+        const double E = (double)std::max<uint64_t>(p->nent, 1);
+        uint64_t ys = (uint64_t)std::min(std::sqrt(acc / 2.0),
+                                         std::sqrt(4.0 * kGatherTile * acc / E));
         const char *e = getenv("MERTENS_GATHER_END");
-        uint64_t ys = e ? strtoull(e, nullptr, 10) : (1ull << 28);
+        if (e)
+            ys = strtoull(e, nullptr, 10);
         p->gather_smem_end = std::min(ys, p->y_max);
     }
     std::vector<GatherTile> gtiles;
     std::vector<GatherItem> gitems;
+    std::vector<std::pair<uint64_t, uint64_t>> ranges;
     for (uint64_t b = 0; b < p->nblocks; ++b) {
         const uint64_t y1 = 1 + b * block_len;
         const uint64_t y2 = std::min(y1 + block_len - 1, p->y_max);
@@ -465,7 +485,11 @@ int mertens_plan(mertens_plan_t *out, const mertens_u128 *n, size_t count, merte
             T.l2 = magic_shift(t2 + 1);
             T.pad = 0;
             const uint32_t ti = (uint32_t)gtiles.size();
-            bool used = false;
+            // entries that can have terms here: per target the suffix whose
+            // cut-off lies below t2 (found on the running minimum); suffixes
+            // of consecutive targets separated by short gaps are merged (an
+            // entry outside its suffix simply has no terms in the tile)
+            ranges.clear();
             for (size_t i = 0; i < count; ++i) {
                 const uint64_t o = p->off[i], X = p->X[i];
                 uint64_t lo = 0, hi = X;  // first x index with ycmin < t2
@@ -476,28 +500,35 @@ int mertens_plan(mertens_plan_t *out, const mertens_u128 *n, size_t count, merte
                     else
                         lo = mid + 1;
                 }
-                // work of entries [f, g): about one range check each plus
-                // sum k * len / t1^2 gathered terms; items of ~kItemWork
-                const double per_k = (double)T.len / ((double)t1 * (double)t1);
-                for (uint64_t f = lo; f < X;) {
-                    uint64_t g = std::min<uint64_t>(f + 1024, X);
-                    while (g < X) {
-                        const double work = (double)(g - f) + per_k * (kpre[o + g] - kpre[o + f]);
+                if (lo >= X)
+                    continue;
+                if (!ranges.empty() && o + lo <= ranges.back().second + 4096)
+                    ranges.back().second = o + X;
+                else
+                    ranges.push_back({o + lo, o + X});
+            }
+            // work of entries [f, g): about one range check each plus
+            // sum k * len / t1^2 gathered terms; items of ~kItemWork
+            const double per_k = (double)T.len / ((double)t1 * (double)t1);
+            for (const auto &rg : ranges) {
+                for (uint64_t f = rg.first; f < rg.second;) {
+                    uint64_t g = std::min<uint64_t>(f + 1024, rg.second);
+                    while (g < rg.second) {
+                        const double work = (double)(g - f) + per_k * (kpre[g] - kpre[f]);
                         if (work >= kItemWork)
                             break;
-                        g = std::min<uint64_t>(g + 1024, X);
+                        g = std::min<uint64_t>(g + 1024, rg.second);
                     }
                     GatherItem it;
                     it.tile = ti;
-                    it.e0 = (uint32_t)(o + f);
-                    it.e1 = (uint32_t)(o + g);
+                    it.e0 = (uint32_t)f;
+                    it.e1 = (uint32_t)g;
                     it.pad = 0;
                     gitems.push_back(it);
-                    used = true;
                     f = g;
                 }
             }
-            if (used)
+            if (!ranges.empty())
                 gtiles.push_back(T);
         }
     }
@@ -636,15 +667,9 @@ static void clear_events(mertens_plan_s *p)
     p->prof_runs = 0;
 }
 
-int mertens_run(mertens_plan_t p, void *stream)
+// Enqueues one whole run (all blocks, then resolve) on s; *out = kernels.
+static int run_enqueue(mertens_plan_s *p, cudaStream_t s, uint64_t *out)
 {
-    if (!p) {
-        set_last_error("mertens_run: NULL plan");
-        return MERTENS_EINVAL;
-    }
-    cudaStream_t s = (cudaStream_t)stream;
-    PhaseEvents total;
-    ev_begin(p, kPhTotal, s, &total);
     uint64_t launches = 0;
     int r;
     const size_t E = p->nent;
@@ -779,18 +804,81 @@ int mertens_run(mertens_plan_t p, void *stream)
             goto fail;
         launches += r;
     }
-    ev_end(p, s, &total);
-    if (p->prof)
-        ++p->prof_runs;
-    if (cudaEventRecord(p->done, s) != cudaSuccess)
-        goto fail;
-    p->kernels = launches;
-    p->d2h_bytes = 0;
-    p->ran = true;
+    *out = launches;
     return MERTENS_OK;
 fail:
     set_last_error("mertens_run: launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     return MERTENS_ECUDA;
+}
+
+// Whole runs after the first are replayed from a CUDA graph captured on the
+// plan's own stream (kernel arguments of a plan never change between runs),
+// unless profiling is on or MERTENS_NO_GRAPH is set.
+int mertens_run(mertens_plan_t p, void *stream)
+{
+    if (!p) {
+        set_last_error("mertens_run: NULL plan");
+        return MERTENS_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    uint64_t launches = 0;
+    const bool graph_ok = !p->prof && p->mg_built && !getenv("MERTENS_NO_GRAPH");
+    if (!graph_ok) {
+        PhaseEvents total;
+        ev_begin(p, kPhTotal, s, &total);
+        const int rc = run_enqueue(p, s, &launches);
+        if (rc != MERTENS_OK)
+            return rc;
+        ev_end(p, s, &total);
+        if (p->prof)
+            ++p->prof_runs;
+    } else {
+        if (!p->gexec) {
+            if (!p->cap_stream &&
+                cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+                set_last_error("mertens_run: cannot create the capture stream");
+                return MERTENS_ECUDA;
+            }
+            if (cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal) !=
+                cudaSuccess) {
+                set_last_error("mertens_run: cannot begin capture: %s",
+                               cudaGetErrorString(cudaGetLastError()));
+                return MERTENS_ECUDA;
+            }
+            const int rc = run_enqueue(p, p->cap_stream, &launches);
+            cudaGraph_t g = nullptr;
+            const cudaError_t ce = cudaStreamEndCapture(p->cap_stream, &g);
+            if (rc != MERTENS_OK || ce != cudaSuccess || !g) {
+                if (g)
+                    cudaGraphDestroy(g);
+                set_last_error("mertens_run: capture failed: %s", cudaGetErrorString(ce));
+                return MERTENS_ECUDA;
+            }
+            const cudaError_t ie = cudaGraphInstantiate(&p->gexec, g, 0);
+            cudaGraphDestroy(g);
+            if (ie != cudaSuccess) {
+                p->gexec = nullptr;
+                set_last_error("mertens_run: graph instantiation failed: %s",
+                               cudaGetErrorString(ie));
+                return MERTENS_ECUDA;
+            }
+            p->graph_kernels = launches;
+        }
+        if (cudaGraphLaunch(p->gexec, s) != cudaSuccess) {
+            set_last_error("mertens_run: graph launch failed: %s",
+                           cudaGetErrorString(cudaGetLastError()));
+            return MERTENS_ECUDA;
+        }
+        launches = p->graph_kernels;
+    }
+    if (cudaEventRecord(p->done, s) != cudaSuccess) {
+        set_last_error("mertens_run: %s", cudaGetErrorString(cudaGetLastError()));
+        return MERTENS_ECUDA;
+    }
+    p->kernels = launches;
+    p->d2h_bytes = 0;
+    p->ran = true;
+    return MERTENS_OK;
 }
 
 int mertens_result(mertens_plan_t p, size_t i, int64_t *M_n, int64_t *entries, size_t cap,
@@ -841,6 +929,10 @@ void mertens_destroy(mertens_plan_t p)
         cudaEventDestroy(p->done);
     }
     clear_events(p);
+    if (p->gexec)
+        cudaGraphExecDestroy(p->gexec);
+    if (p->cap_stream)
+        cudaStreamDestroy(p->cap_stream);
     if (p->pt.np)
         prime_table_destroy(&p->pt);
     for (auto &a : p->allocs)

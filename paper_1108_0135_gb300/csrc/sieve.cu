@@ -46,11 +46,12 @@ struct SieveArgs {
 // tile, and c = (that multiple / p) mod p, which is 0 exactly when p^2 divides
 // the multiple.  Uses y1 mod p and floor(y1/p) mod p of the block.
 __device__ __forceinline__ void first_multiple(const SieveArgs &a, uint32_t t, uint64_t a0,
-                                               uint32_t &p, uint32_t &off, uint32_t &c)
+                                               uint32_t &p, uint32_t &off, uint32_t &c,
+                                               uint64_t &m, unsigned &l)
 {
     p = a.p[t];
-    const uint64_t m = a.m[t];
-    const unsigned l = a.l[t];
+    m = a.m[t];
+    l = a.l[t];
     const uint64_t v = (uint64_t)a.r[t] + a0;       // t1 - floor(y1/p)*p
     const uint64_t qv = div_magic(v << 1, m, l);     // floor(v / p)
     const uint32_t off0 = (uint32_t)(v - qv * p);    // t1 mod p
@@ -81,15 +82,24 @@ __device__ __forceinline__ void sieve_prime_warp(const SieveArgs &a, uint32_t *w
                                                  uint64_t a0, uint32_t lo, uint32_t hi, int lane)
 {
     uint32_t p, off, c;
-    first_multiple(a, t, a0, p, off, c);
+    uint64_t m;
+    unsigned l;
+    first_multiple(a, t, a0, p, off, c, m, l);
     if (off < lo) {
-        const uint32_t steps = (lo - off + p - 1) / p;
-        off += steps * p;
-        c = (c + steps) % p;
+        // steps = ceil((lo - off) / p); c = (c + steps) mod p, by the magic of p
+        const uint64_t steps = div_magic((uint64_t)(lo - off + p - 1) << 1, m, l);
+        off += (uint32_t)steps * p;
+        const uint64_t cs = (uint64_t)c + steps;
+        c = (uint32_t)(cs - div_magic(cs << 1, m, l) * p);
     }
     const uint32_t add = a.lg[t] | kCountOne;
-    uint32_t ci = (c + (uint32_t)lane) % p;
-    const uint32_t inc = 32u % p;
+    // (c + lane) mod p and 32 mod p with p >= 11: at most three subtractions
+    uint32_t ci = c + (uint32_t)lane;
+    while (ci >= p)
+        ci -= p;
+    uint32_t inc = 32u;
+    while (inc >= p)
+        inc -= p;
     for (uint32_t yo = off + (uint32_t)lane * p; yo < hi; yo += 32u * p) {
         const uint32_t sh = (yo & 1u) << 4;
         atomicAdd(&w[yo >> 1], add << sh);
@@ -167,7 +177,9 @@ __global__ void __launch_bounds__(kSieveThreads, 1) mu_sieve_kernel(SieveArgs a)
             const uint32_t t = a.np_small + (job - js) * 32u + (uint32_t)lane;
             if (t < a.np) {
                 uint32_t p, off, c;
-                first_multiple(a, t, a0, p, off, c);
+                uint64_t m;
+                unsigned l;
+                first_multiple(a, t, a0, p, off, c, m, l);
                 const uint32_t add = a.lg[t] | kCountOne;
                 for (uint32_t yo = off; yo < tl; yo += p) {
                     const uint32_t sh = (yo & 1u) << 4;

@@ -201,6 +201,37 @@ def test_result_before_run_is_not_ready():
         pm.mertens_destroy(plan)
 
 
+# ---- Table 1 values beyond 10^16 ----------------------------------------------
+
+def test_table1_1e18_auto_parameters(table1):
+    m, arr = gpu_array(10**18)
+    assert m == table1[10**18] == -46758740
+    # the array's last entry, k = floor(n/X) ~ 1.1e12, by the oracle recursion
+    k = 10**18 // len(arr)
+    assert arr[-1] == oracle.mertens(k, L=2 * 10**7)
+
+
+def test_batch_of_close_targets_1e17(table1):
+    # Sec. 2: close values share one sieve pass; n_0 = 10^17 is in Table 1
+    ns = [10**17 + i * 10**9 for i in range(8)]
+    plan = pm.mertens_plan(ns)
+    try:
+        pm.mertens_run(plan)
+        res = [pm.mertens_result(plan, i, entries=True) for i in range(len(ns))]
+        infos = [pm.mertens_plan_info(plan, i) for i in range(len(ns))]
+    finally:
+        pm.mertens_destroy(plan)
+    assert res[0][0] == table1[10**17] == -21830254
+    # the same target alone, with the batch's u, gives the same array
+    for i in (0, 5):
+        m1, arr1 = gpu_array(ns[i], infos[i]["u"])
+        assert res[i][0] == m1 and np.array_equal(res[i][1], arr1)
+    # the last entry (smallest k ~ 8e11) of two more targets by the oracle
+    for i in (3, 7):
+        X = len(res[i][1])
+        assert res[i][1][X - 1] == oracle.mertens(ns[i] // X, L=10**8), i
+
+
 # ---- full size: n = 10^16, u = 4e10, block 2^28 ------------------------------
 
 def test_table1_1e16_full_configuration(table1):
