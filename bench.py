@@ -47,7 +47,9 @@ def parse_args():
                     help="skip the timed oracle sample (cpu_baseline key)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-extra", action="store_true",
-                    help="skip the one-shot M(10^18) wall-time measurement")
+                    help="skip the M(10^18) wall time and the serving measurement")
+    ap.add_argument("--serve-sample", type=int, default=240,
+                    help="queries of the seeded serving stream measured (extra key)")
     return ap.parse_args()
 
 
@@ -224,6 +226,36 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def serving_measure(sample: int):
+    """Batched-query latency: the first `sample` queries of the seeded
+    10^4-query stream (n log-uniform in [10^10, 10^16]) through the native
+    continuous-batching server, closed loop (all submitted at once) and open
+    loop (Poisson arrivals at 0.8 x the closed-loop rate), against the same
+    queries run one plan each."""
+    from paper_1108_0135_gb300 import serve, workloads
+
+    _, ns = workloads.serving_stream(seed=20261203, count=10_000)
+    ns = [int(v) for v in ns[:sample]]
+    one = serve.run_one_per_plan(ns)
+    closed = serve.run_stream(ns)
+    assert closed["answers"] == one["answers"]
+    rate = 0.8 * closed["queries_per_s"]
+    arr = np.cumsum(np.random.default_rng(20261203).exponential(1.0 / rate, size=len(ns)))
+    opened = serve.run_stream(ns, arrivals_s=arr)
+    assert opened["answers"] == one["answers"]
+    return {
+        "sample": f"first {len(ns)} of the seeded 10^4-query stream, n log-uniform in "
+                  f"[1e10, 1e16]",
+        "one_plan_per_query_qps": one["queries_per_s"],
+        "closed_loop": {"qps": closed["queries_per_s"], "p50_s": closed["p50_s"],
+                        "p99_s": closed["p99_s"], "batches": closed["stats"]["batches"],
+                        "max_inflight": closed["stats"]["max_inflight"]},
+        "open_loop": {"rate_qps": rate, "qps": opened["queries_per_s"],
+                      "p50_s": opened["p50_s"], "p99_s": opened["p99_s"]},
+        "batched_over_one_per_plan": closed["queries_per_s"] / one["queries_per_s"],
+    }
+
+
 def run_native(args, world, rank, local):
     import torch
 
@@ -302,6 +334,8 @@ def run_native(args, world, rank, local):
                            "u": i18["u"], "X": i18["X"],
                            "update_terms_per_s": (i18["direct_terms"] + i18["gathered_terms"])
                            / t18}
+        extra["serving"] = serving_measure(args.serve_sample)
+
 
     # e2e: the user call with host inputs and host results, every step
     host_out = torch.empty(info["X"], dtype=torch.int64, pin_memory=True)

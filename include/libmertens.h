@@ -52,8 +52,10 @@ const char *mertens_strerror(int code);
 const char *mertens_last_error(void);
 
 /*
- * Device-memory hook.  By default the library allocates with cudaMalloc and
- * frees with cudaFree.  A caller (for example a PyTorch process that wants
+ * Device-memory hook.  By default the library allocates stream-ordered
+ * (cudaMallocAsync / cudaFreeAsync on a non-blocking library stream, then
+ * waits for that stream alone), so plans can be created and destroyed while
+ * other work runs on the device.  A caller (for example a PyTorch process that wants
  * the caching allocator) may install its own pair; `ctx` is passed back
  * unchanged.  alloc must return 256-byte aligned device memory or NULL.
  * Passing alloc = NULL restores the default.  Applies to plans created after
@@ -200,6 +202,56 @@ int mertens_sieve_mu(uint64_t y1, uint64_t len, int8_t *mu_dev, void *stream);
  */
 int mertens_sieve_M(uint64_t y1, uint64_t len, int64_t carry, int32_t *M_dev,
                     void *stream);
+
+/* ---- serving: continuous batching of M(n) queries ---------------------- */
+
+/*
+ * A server owns one worker thread on `device`.  Queries are submitted from
+ * any host thread and answered asynchronously.  The worker groups waiting
+ * queries of the same magnitude (floor(log2 n)) into batches of at most
+ * `max_batch` targets -- one plan, one shared sieve pass per batch (Sec. 2:
+ * close values share the sieve) -- and keeps up to `max_inflight` batches
+ * running at once, each on its own stream, admitting a new batch whenever a
+ * slot is free and its estimated device memory fits what is left of
+ * `mem_budget_bytes`.  Queries that arrive while others run on the GPU are
+ * admitted as slots and memory free up; their work overlaps on the device.
+ * Results are exact and do not depend on how queries were batched.
+ *
+ *   mertens_server_create: device >= 0; mem_budget_bytes = 0 means 80% of the
+ *     free device memory; max_inflight 1..16 (0 = 4); max_batch 1..4096
+ *     (0 = 64).  Errors: MERTENS_EINVAL, MERTENS_ECUDA, MERTENS_ENOMEM.
+ *   mertens_server_submit: 1 <= n < 2^63 (else MERTENS_ENOTSUP / EINVAL);
+ *     *ticket receives the query's id.
+ *   mertens_server_poll: MERTENS_OK with *M_n set once the answer is there,
+ *     MERTENS_ENOTREADY before, MERTENS_EINVAL for an unknown ticket, or the
+ *     status the query's batch failed with.
+ *   mertens_server_wait: blocks up to timeout_s (< 0: forever); MERTENS_ETIMEOUT
+ *     when it runs out.
+ *   mertens_server_times: host steady-clock nanoseconds of submission and of
+ *     the answer (0 if not answered yet).
+ *   mertens_server_destroy: finishes the admitted batches, drops queries
+ *     still waiting, joins the worker and frees everything.
+ */
+typedef struct mertens_server_s *mertens_server_t;
+
+typedef struct {
+    uint64_t submitted;      /* queries submitted                          */
+    uint64_t answered;       /* queries answered                           */
+    uint64_t batches;        /* batches (plans) run                        */
+    uint64_t max_inflight;   /* most batches in flight at once             */
+    uint64_t max_batch_seen; /* largest batch                              */
+    uint64_t failed;         /* queries whose batch failed                 */
+} mertens_server_stats;
+
+int mertens_server_create(mertens_server_t *out, int device, size_t mem_budget_bytes,
+                          uint32_t max_inflight, uint32_t max_batch);
+int mertens_server_submit(mertens_server_t srv, mertens_u128 n, uint64_t *ticket);
+int mertens_server_poll(mertens_server_t srv, uint64_t ticket, int64_t *M_n);
+int mertens_server_wait(mertens_server_t srv, uint64_t ticket, int64_t *M_n, double timeout_s);
+int mertens_server_times(mertens_server_t srv, uint64_t ticket, uint64_t *t_submit_ns,
+                         uint64_t *t_done_ns);
+int mertens_server_stats_get(mertens_server_t srv, mertens_server_stats *stats);
+void mertens_server_destroy(mertens_server_t srv);
 
 /*
  * mertens_sieve_M_noalloc -- the same result as mertens_sieve_M (M(y) for

@@ -10,7 +10,8 @@ from ._lib import (  # noqa: F401
     MERTENS_ETIMEOUT, MERTENS_OK, MertensError, load, mertens, mertens_describe, mertens_destroy,
     mertens_last_error, mertens_plan, mertens_plan_info, mertens_plan_set_profiling,
     mertens_result, mertens_result_into, mertens_run, mertens_run_stats_get,
+    mertens_server_create, mertens_server_destroy, mertens_server_poll, mertens_server_stats_get,
+    mertens_server_submit, mertens_server_times, mertens_server_wait,
     mertens_set_allocator, mertens_sieve_M, mertens_sieve_M_noalloc, mertens_sieve_mu,
-    mertens_strerror,
-    use_torch_allocator,
+    mertens_strerror, use_torch_allocator,
 )

@@ -56,7 +56,16 @@ EXPORTS = [
     "mertens_run", "mertens_result", "mertens_destroy", "mertens_describe",
     "mertens_plan_info", "mertens_plan_set_profiling", "mertens_run_stats_get",
     "mertens_sieve_mu", "mertens_sieve_M", "mertens_sieve_M_noalloc",
+    "mertens_server_create", "mertens_server_submit", "mertens_server_poll",
+    "mertens_server_wait", "mertens_server_times", "mertens_server_stats_get",
+    "mertens_server_destroy",
 ]
+
+
+class mertens_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("answered", ctypes.c_uint64),
+                ("batches", ctypes.c_uint64), ("max_inflight", ctypes.c_uint64),
+                ("max_batch_seen", ctypes.c_uint64), ("failed", ctypes.c_uint64)]
 
 _lock = threading.Lock()
 _lib = None
@@ -109,6 +118,21 @@ def load():
         lib.mertens_sieve_M.restype = c_int
         lib.mertens_sieve_M_noalloc.argtypes = [u64, u64, i64, P, P]
         lib.mertens_sieve_M_noalloc.restype = c_int
+        u32 = ctypes.c_uint32
+        lib.mertens_server_create.argtypes = [ctypes.POINTER(P), c_int, sz, u32, u32]
+        lib.mertens_server_create.restype = c_int
+        lib.mertens_server_submit.argtypes = [P, mertens_u128, ctypes.POINTER(u64)]
+        lib.mertens_server_submit.restype = c_int
+        lib.mertens_server_poll.argtypes = [P, u64, ctypes.POINTER(i64)]
+        lib.mertens_server_poll.restype = c_int
+        lib.mertens_server_wait.argtypes = [P, u64, ctypes.POINTER(i64), ctypes.c_double]
+        lib.mertens_server_wait.restype = c_int
+        lib.mertens_server_times.argtypes = [P, u64, ctypes.POINTER(u64), ctypes.POINTER(u64)]
+        lib.mertens_server_times.restype = c_int
+        lib.mertens_server_stats_get.argtypes = [P, ctypes.POINTER(mertens_server_stats)]
+        lib.mertens_server_stats_get.restype = c_int
+        lib.mertens_server_destroy.argtypes = [P]
+        lib.mertens_server_destroy.restype = None
         _lib = lib
         return lib
 
@@ -248,6 +272,57 @@ def mertens_sieve_M_noalloc(y1: int, length: int, carry: int, M_dev, stream=None
     len <= 2^21, y1 + len - 1 < 2^40; overlapping calls race)."""
     _check(load().mertens_sieve_M_noalloc(int(y1), int(length), int(carry), _ptr(M_dev),
                                           _stream(stream)), "mertens_sieve_M_noalloc")
+
+
+def mertens_server_create(device: int = 0, mem_budget_bytes: int = 0, max_inflight: int = 0,
+                          max_batch: int = 0) -> int:
+    h = ctypes.c_void_p()
+    _check(load().mertens_server_create(ctypes.byref(h), int(device), int(mem_budget_bytes),
+                                        int(max_inflight), int(max_batch)),
+           "mertens_server_create")
+    return int(h.value)
+
+
+def mertens_server_submit(srv: int, n: int) -> int:
+    t = ctypes.c_uint64()
+    _check(load().mertens_server_submit(srv, u128(n), ctypes.byref(t)), "mertens_server_submit")
+    return int(t.value)
+
+
+def mertens_server_poll(srv: int, ticket: int):
+    """M(n) of the ticket's query, or None while it is not answered yet."""
+    m = ctypes.c_int64()
+    rc = load().mertens_server_poll(srv, int(ticket), ctypes.byref(m))
+    if rc == MERTENS_ENOTREADY:
+        return None
+    _check(rc, "mertens_server_poll")
+    return int(m.value)
+
+
+def mertens_server_wait(srv: int, ticket: int, timeout_s: float = -1.0) -> int:
+    m = ctypes.c_int64()
+    _check(load().mertens_server_wait(srv, int(ticket), ctypes.byref(m), float(timeout_s)),
+           "mertens_server_wait")
+    return int(m.value)
+
+
+def mertens_server_times(srv: int, ticket: int):
+    """(submit_ns, done_ns) on the host steady clock; done_ns = 0 if pending."""
+    a, b = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load().mertens_server_times(srv, int(ticket), ctypes.byref(a), ctypes.byref(b)),
+           "mertens_server_times")
+    return int(a.value), int(b.value)
+
+
+def mertens_server_stats_get(srv: int) -> dict:
+    st = mertens_server_stats()
+    _check(load().mertens_server_stats_get(srv, ctypes.byref(st)), "mertens_server_stats_get")
+    return {name: getattr(st, name) for name, _ in mertens_server_stats._fields_}
+
+
+def mertens_server_destroy(srv: int) -> None:
+    if srv:
+        load().mertens_server_destroy(srv)
 
 
 _alloc_keepalive = []

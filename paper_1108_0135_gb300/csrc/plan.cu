@@ -45,6 +45,34 @@ Allocator current_allocator()
     return a;
 }
 
+// Default device memory: stream-ordered allocation on one non-blocking
+// library stream per device, so that creating or destroying a plan never
+// waits for other work on the device (the allocation is made usable on every
+// stream by waiting for that stream alone).  Freed memory stays in the
+// process's default pool for reuse.
+constexpr int kMaxDevices = 64;
+static cudaStream_t g_alloc_stream[kMaxDevices];
+
+static cudaStream_t alloc_stream()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+        return nullptr;
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    if (!g_alloc_stream[dev]) {
+        cudaStream_t s = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
+            return nullptr;
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t keep = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        g_alloc_stream[dev] = s;
+    }
+    return g_alloc_stream[dev];
+}
+
 void *dev_alloc(const Allocator &a, size_t bytes)
 {
     if (bytes == 0)
@@ -52,21 +80,26 @@ void *dev_alloc(const Allocator &a, size_t bytes)
     if (a.alloc)
         return a.alloc(bytes, nullptr, a.ctx);
     void *p = nullptr;
-    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaStream_t s = alloc_stream();
+    if (!s || cudaMallocAsync(&p, bytes, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
     }
     return p;
 }
 
+// Callers free only memory no queued work still uses.
 void dev_free(const Allocator &a, void *p, size_t bytes)
 {
     if (!p)
         return;
-    if (a.alloc)
+    if (a.alloc) {
         a.release(p, bytes, nullptr, a.ctx);
-    else
-        cudaFree(p);
+        return;
+    }
+    cudaStream_t s = alloc_stream();
+    if (s)
+        cudaFreeAsync(p, s);
 }
 
 static uint64_t isqrt64(uint64_t v)
@@ -193,6 +226,22 @@ static uint64_t auto_u(uint64_t n, size_t count)
         u = n;
     return u;
 }
+
+namespace mert {
+// The sieve limit the library picks for target n in a batch of `count`.
+uint64_t plan_auto_u(uint64_t n, size_t count) { return auto_u(n, count); }
+// Device bytes a plan holds (its buffers and its prime table).
+size_t plan_device_bytes(mertens_plan_t p)
+{
+    if (!p)
+        return 0;
+    size_t b = 0;
+    for (auto &a : p->allocs)
+        b += a.second;
+    b += (size_t)p->pt.np * 25 + 2 * kPatternWords * 4;
+    return b;
+}
+}  // namespace mert
 
 static int check_u(uint64_t n, uint64_t u)
 {

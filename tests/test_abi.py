@@ -70,6 +70,15 @@ def test_invalid_arguments_rejected_without_gpu(n, u, code):
     assert ei.value.code == code
 
 
+def test_server_without_usable_device_fails_cleanly():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(pm.MertensError) as ei:
+        pm.mertens_server_create(0)
+    assert ei.value.code in (pm._lib.MERTENS_ECUDA, pm.MERTENS_EINVAL)
+
+
 def test_plan_rejects_empty_batch():
     lib = pm.load()
     h = ctypes.c_void_p()
