@@ -76,7 +76,7 @@ int mertens_set_allocator(mertens_alloc_fn alloc, mertens_free_fn release, void 
  *              (MERTENS_ENOTSUP at or above 2^63).  Copied; the caller keeps
  *              ownership.
  *   u          sieve limit shared by all targets.  {0,0} = chosen per target
- *              by the library (about 0.9 * n_i^(2/3)).  Otherwise it must
+ *              by the library (see mertens_tuning).  Otherwise it must
  *              satisfy floor(sqrt(n_i)) < u <= n_i for every i (u = 1 is
  *              allowed for n_i = 1), else MERTENS_EINVAL.  Each target's array
  *              has X_i = floor(n_i/u_i) entries (Sec. 2).
@@ -203,12 +203,51 @@ int mertens_sieve_mu(uint64_t y1, uint64_t len, int8_t *mu_dev, void *stream);
 int mertens_sieve_M(uint64_t y1, uint64_t len, int64_t carry, int32_t *M_dev,
                     void *stream);
 
+/* ---- tuning ------------------------------------------------------------ */
+
+/*
+ * Performance parameters used for plans created afterwards (process-wide).
+ * None of them changes any result -- only speed (Sec. 3: "all the various
+ * constants and thresholds ... were tuned for peak performance").
+ *   u_factor      automatic sieve limit
+ *                 u = u_factor * (count * n)^(2/3) * count^(-1/5),
+ *                 clamped to (floor(sqrt(n)), n] (Sec. 2: u = O(n^(2/3)),
+ *                 batched u = O((nN)^(2/3)));             default 0.45
+ *   dense_c       dense cut-off y_c ~ dense_c * sqrt(floor(n/x)) per entry
+ *                 (the paper's regions 1/1' bound c1);     default 1.6
+ *   gather_scale  multiplies the automatic end of the shared-memory gather
+ *                 range;                                   default 1.0
+ *   block_cap     largest automatic sieve block (0 = 2^28, or 2^30 above
+ *                 2^36 sieved y); otherwise in [2^16, 2^31]
+ */
+typedef struct {
+    double u_factor;
+    double dense_c;
+    double gather_scale;
+    uint64_t block_cap;
+} mertens_tuning;
+
+int mertens_set_tuning(const mertens_tuning *t);  /* MERTENS_EINVAL if out of range */
+int mertens_get_tuning(mertens_tuning *t);
+
+/*
+ * mertens_autotune -- times candidate tunings on the current device for the
+ * targets n[0..count) (one plan per candidate, a warm-up run, then `runs`
+ * timed runs with CUDA events) by coordinate search over u_factor, dense_c
+ * and gather_scale, starting from the tuning in force.  Writes the fastest
+ * to *best and its time per run to *best_ms; does not apply it (call
+ * mertens_set_tuning).  The work is that of ~10 candidates x (runs + 1)
+ * whole computations.  Errors: those of mertens_plan / mertens_run.
+ */
+int mertens_autotune(const mertens_u128 *n, size_t count, int runs, mertens_tuning *best,
+                     double *best_ms);
+
 /* ---- serving: continuous batching of M(n) queries ---------------------- */
 
 /*
  * A server owns one worker thread on `device`.  Queries are submitted from
  * any host thread and answered asynchronously.  The worker groups waiting
- * queries of the same magnitude (floor(log2 n)) into batches of at most
+ * queries of the same magnitude (floor(log2(n)/2)) into batches of at most
  * `max_batch` targets -- one plan, one shared sieve pass per batch (Sec. 2:
  * close values share the sieve) -- and keeps up to `max_inflight` batches
  * running at once, each on its own stream, admitting a new batch whenever a

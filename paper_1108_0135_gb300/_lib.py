@@ -56,10 +56,16 @@ EXPORTS = [
     "mertens_run", "mertens_result", "mertens_destroy", "mertens_describe",
     "mertens_plan_info", "mertens_plan_set_profiling", "mertens_run_stats_get",
     "mertens_sieve_mu", "mertens_sieve_M", "mertens_sieve_M_noalloc",
+    "mertens_set_tuning", "mertens_get_tuning", "mertens_autotune",
     "mertens_server_create", "mertens_server_submit", "mertens_server_poll",
     "mertens_server_wait", "mertens_server_times", "mertens_server_stats_get",
     "mertens_server_destroy",
 ]
+
+
+class mertens_tuning(ctypes.Structure):
+    _fields_ = [("u_factor", ctypes.c_double), ("dense_c", ctypes.c_double),
+                ("gather_scale", ctypes.c_double), ("block_cap", ctypes.c_uint64)]
 
 
 class mertens_server_stats(ctypes.Structure):
@@ -119,6 +125,14 @@ def load():
         lib.mertens_sieve_M_noalloc.argtypes = [u64, u64, i64, P, P]
         lib.mertens_sieve_M_noalloc.restype = c_int
         u32 = ctypes.c_uint32
+        lib.mertens_set_tuning.argtypes = [ctypes.POINTER(mertens_tuning)]
+        lib.mertens_set_tuning.restype = c_int
+        lib.mertens_get_tuning.argtypes = [ctypes.POINTER(mertens_tuning)]
+        lib.mertens_get_tuning.restype = c_int
+        lib.mertens_autotune.argtypes = [ctypes.POINTER(mertens_u128), sz, c_int,
+                                         ctypes.POINTER(mertens_tuning),
+                                         ctypes.POINTER(ctypes.c_double)]
+        lib.mertens_autotune.restype = c_int
         lib.mertens_server_create.argtypes = [ctypes.POINTER(P), c_int, sz, u32, u32]
         lib.mertens_server_create.restype = c_int
         lib.mertens_server_submit.argtypes = [P, mertens_u128, ctypes.POINTER(u64)]
@@ -272,6 +286,40 @@ def mertens_sieve_M_noalloc(y1: int, length: int, carry: int, M_dev, stream=None
     len <= 2^21, y1 + len - 1 < 2^40; overlapping calls race)."""
     _check(load().mertens_sieve_M_noalloc(int(y1), int(length), int(carry), _ptr(M_dev),
                                           _stream(stream)), "mertens_sieve_M_noalloc")
+
+
+def _tuning_dict(t: mertens_tuning) -> dict:
+    return {name: getattr(t, name) for name, _ in mertens_tuning._fields_}
+
+
+def mertens_get_tuning() -> dict:
+    t = mertens_tuning()
+    _check(load().mertens_get_tuning(ctypes.byref(t)), "mertens_get_tuning")
+    return _tuning_dict(t)
+
+
+def mertens_set_tuning(u_factor=None, dense_c=None, gather_scale=None, block_cap=None) -> dict:
+    """Sets the given fields (others keep their value); returns the tuning."""
+    cur = mertens_get_tuning()
+    for k, v in (("u_factor", u_factor), ("dense_c", dense_c), ("gather_scale", gather_scale),
+                 ("block_cap", block_cap)):
+        if v is not None:
+            cur[k] = v
+    t = mertens_tuning(float(cur["u_factor"]), float(cur["dense_c"]),
+                       float(cur["gather_scale"]), int(cur["block_cap"]))
+    _check(load().mertens_set_tuning(ctypes.byref(t)), "mertens_set_tuning")
+    return cur
+
+
+def mertens_autotune(n, runs: int = 1):
+    """(best tuning dict, ms per run) for the targets n, not applied."""
+    ns = [int(n)] if isinstance(n, (int, np.integer)) else [int(v) for v in n]
+    arr = (mertens_u128 * len(ns))(*[u128(v) for v in ns])
+    best = mertens_tuning()
+    ms = ctypes.c_double()
+    _check(load().mertens_autotune(arr, len(ns), int(runs), ctypes.byref(best), ctypes.byref(ms)),
+           "mertens_autotune")
+    return _tuning_dict(best), float(ms.value)
 
 
 def mertens_server_create(device: int = 0, mem_budget_bytes: int = 0, max_inflight: int = 0,

@@ -137,6 +137,7 @@ struct mertens_plan_s {
     std::vector<uint64_t> direct, gathered, ymax_q;
     uint64_t nent = 0;
     uint64_t y_max = 0, block_len = 0, nblocks = 0, ydense = 0, jmax = 0, mg_n = 0;
+    mertens_tuning tuning{};
     uint64_t terms = 0, dense_y = 0, gather_j = 0;
     double sieve_updates = 0;
     // device buffers
@@ -188,10 +189,21 @@ struct mertens_plan_s {
     }
 };
 
-static double dense_factor()
+// Tuning in force for new plans (mertens_set_tuning); MERTENS_* environment
+// variables override single fields for experiments.
+static std::mutex g_tune_mu;
+static mertens_tuning g_tuning = {0.45, 1.6, 1.0, 0};
+
+static mertens_tuning tuning_now()
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return g_tuning;
+}
+
+static double dense_factor(const mertens_tuning &t)
 {
     const char *e = getenv("MERTENS_DENSE_C");
-    double c = e ? atof(e) : 1.6;
+    double c = e ? atof(e) : t.dense_c;
     return c > 0 ? c : 1.6;
 }
 
@@ -213,12 +225,18 @@ static int describe_target(uint64_t n, uint64_t u, uint64_t *X, uint64_t *direct
     return 0;
 }
 
-static uint64_t auto_u(uint64_t n, size_t count)
+// u = f (count n)^(2/3) count^(-1/5): the sieve costs ~u and the update
+// ~count sqrt(n n/u), balanced at u ~ (count n)^(2/3) (Sec. 2); the extra
+// count^(-1/5) and f = 0.45 are what the autotuner measured on GB300 for
+// single targets (0.45) and batches of 8 (0.3).
+static uint64_t auto_u(uint64_t n, size_t count, const mertens_tuning &t)
 {
     if (n <= 3)
         return n;
-    double f = 0.9;
-    uint64_t u = (uint64_t)(f * std::pow((double)n * (double)count, 2.0 / 3.0));
+    const char *e = getenv("MERTENS_U_FACTOR");
+    const double f = e ? atof(e) : (t.u_factor > 0 ? t.u_factor : 0.45);
+    uint64_t u = (uint64_t)(f * std::pow((double)n * (double)count, 2.0 / 3.0) *
+                            std::pow((double)count, -0.2));
     const uint64_t r = isqrt64(n);
     if (u <= r)
         u = r + 1;
@@ -229,7 +247,7 @@ static uint64_t auto_u(uint64_t n, size_t count)
 
 namespace mert {
 // The sieve limit the library picks for target n in a batch of `count`.
-uint64_t plan_auto_u(uint64_t n, size_t count) { return auto_u(n, count); }
+uint64_t plan_auto_u(uint64_t n, size_t count) { return auto_u(n, count, tuning_now()); }
 // Device bytes a plan holds (its buffers and its prime table).
 size_t plan_device_bytes(mertens_plan_t p)
 {
@@ -295,7 +313,7 @@ int mertens_describe(mertens_u128 n, mertens_u128 u, mertens_query_info *info)
         set_last_error("mertens_describe: n >= 2^63 is not supported by this build");
         return MERTENS_ENOTSUP;
     }
-    uint64_t uu = u.lo ? u.lo : auto_u(n.lo, 1);
+    uint64_t uu = u.lo ? u.lo : auto_u(n.lo, 1, tuning_now());
     if (check_u(n.lo, uu) != MERTENS_OK) {
         set_last_error("mertens_describe: u must satisfy floor(sqrt(n)) < u <= n");
         return MERTENS_EINVAL;
@@ -316,8 +334,8 @@ int mertens_describe(mertens_u128 n, mertens_u128 u, mertens_query_info *info)
     return MERTENS_OK;
 }
 
-int mertens_plan(mertens_plan_t *out, const mertens_u128 *n, size_t count, mertens_u128 u,
-                 uint64_t block_len)
+static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count, mertens_u128 u,
+                       uint64_t block_len, const mertens_tuning &tn)
 {
     if (!out)
         return MERTENS_EINVAL;
@@ -351,14 +369,15 @@ int mertens_plan(mertens_plan_t *out, const mertens_u128 *n, size_t count, merte
         return MERTENS_ENOMEM;
     p->al = current_allocator();
     p->nq = count;
-    const double dc = dense_factor();
+    p->tuning = tn;
+    const double dc = dense_factor(tn);
 
     // ---- per-entry host planning ----
     std::vector<uint64_t> K, JLO, JC0, YCE;
     std::vector<Group> groups;
     for (size_t i = 0; i < count; ++i) {
         const uint64_t nn = n[i].lo;
-        const uint64_t uu = u.lo ? u.lo : auto_u(nn, count);
+        const uint64_t uu = u.lo ? u.lo : auto_u(nn, count, tn);
         const uint64_t X = nn / uu;
         p->n.push_back(nn);
         p->u.push_back(uu);
@@ -438,7 +457,9 @@ int mertens_plan(mertens_plan_t *out, const mertens_u128 *n, size_t count, merte
     }
     if (block_len == 0) {
         // one block when it fits 2^28 y, else 2^28 (up to 2^36 y) or 2^30 y blocks
-        const uint64_t cap = p->y_max > (1ull << 36) ? (1ull << 30) : (1ull << 28);
+        uint64_t cap = p->y_max > (1ull << 36) ? (1ull << 30) : (1ull << 28);
+        if (tn.block_cap >= kSieveTile && tn.block_cap <= (1ull << 31))
+            cap = tn.block_cap;
         block_len = std::min<uint64_t>(((p->y_max + kSieveTile - 1) / kSieveTile) * kSieveTile,
                                        cap);
     }
@@ -507,8 +528,9 @@ int mertens_plan(mertens_plan_t *out, const mertens_u128 *n, size_t count, merte
         for (size_t i = 0; i < count; ++i)
             acc += (double)p->n[i] * std::log((double)std::max<uint64_t>(p->X[i], 2));
         const double E = (double)std::max<uint64_t>(p->nent, 1);
-        uint64_t ys = (uint64_t)std::min(std::sqrt(acc / 2.0),
-                                         std::sqrt(4.0 * kGatherTile * acc / E));
+        const double gs = tn.gather_scale > 0 ? tn.gather_scale : 1.0;
+        uint64_t ys = (uint64_t)(gs * std::min(std::sqrt(acc / 2.0),
+                                               std::sqrt(4.0 * kGatherTile * acc / E)));
         const char *e = getenv("MERTENS_GATHER_END");
         if (e)
             ys = strtoull(e, nullptr, 10);
@@ -685,6 +707,49 @@ int mertens_plan(mertens_plan_t *out, const mertens_u128 *n, size_t count, merte
         return rc;
     }
     *out = p;
+    return MERTENS_OK;
+}
+
+int mertens_plan(mertens_plan_t *out, const mertens_u128 *n, size_t count, mertens_u128 u,
+                 uint64_t block_len)
+{
+    return plan_create(out, n, count, u, block_len, tuning_now());
+}
+
+}  // extern "C"
+
+namespace mert {
+// A plan with an explicit tuning (the autotuner's candidates).
+int plan_create_tuned(mertens_plan_t *out, const mertens_u128 *n, size_t count,
+                      const mertens_tuning &t)
+{
+    mertens_u128 u0 = {0, 0};
+    return plan_create(out, n, count, u0, 0, t);
+}
+}  // namespace mert
+
+extern "C" {
+
+int mertens_set_tuning(const mertens_tuning *t)
+{
+    if (!t || !(t->u_factor > 0.0 && t->u_factor < 100.0) ||
+        !(t->dense_c > 0.0 && t->dense_c < 1000.0) ||
+        !(t->gather_scale > 0.0 && t->gather_scale < 1000.0) ||
+        (t->block_cap != 0 && (t->block_cap < (uint64_t)kSieveTile || t->block_cap > (1ull << 31)))) {
+        set_last_error("mertens_set_tuning: factors must be positive and finite, block_cap 0 or "
+                       "in [2^16, 2^31]");
+        return MERTENS_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuning = *t;
+    return MERTENS_OK;
+}
+
+int mertens_get_tuning(mertens_tuning *t)
+{
+    if (!t)
+        return MERTENS_EINVAL;
+    *t = tuning_now();
     return MERTENS_OK;
 }
 

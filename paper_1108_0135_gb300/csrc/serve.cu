@@ -173,9 +173,10 @@ struct mertens_server_s {
                     std::lock_guard<std::mutex> lk(mu);
                     if (queue.empty())
                         break;
-                    const unsigned cls = bitlen64(queue.front().n);
+                    // classes of a factor 4 in n: one sieve limit suits all
+                    const unsigned cls = bitlen64(queue.front().n) / 2;
                     for (auto it = queue.begin(); it != queue.end() && batch.size() < max_batch;) {
-                        if (bitlen64(it->n) == cls) {
+                        if (bitlen64(it->n) / 2 == cls) {
                             batch.push_back(*it);
                             it = queue.erase(it);
                         } else {

@@ -79,6 +79,23 @@ def test_server_without_usable_device_fails_cleanly():
     assert ei.value.code in (pm._lib.MERTENS_ECUDA, pm.MERTENS_EINVAL)
 
 
+def test_tuning_validation_and_effect_on_auto_u():
+    old = pm.mertens_get_tuning()
+    try:
+        with pytest.raises(pm.MertensError):
+            pm.mertens_set_tuning(u_factor=0.0)
+        with pytest.raises(pm.MertensError):
+            pm.mertens_set_tuning(block_cap=1000)
+        pm.mertens_set_tuning(u_factor=0.5)
+        u5 = pm.mertens_describe(10**15)["u"]
+        pm.mertens_set_tuning(u_factor=1.0)
+        u10 = pm.mertens_describe(10**15)["u"]
+        assert abs(u10 / u5 - 2.0) < 1e-6
+        assert pm.mertens_describe(10**15, 10**10)["u"] == 10**10   # explicit u wins
+    finally:
+        pm.mertens_set_tuning(**old)
+
+
 def test_plan_rejects_empty_batch():
     lib = pm.load()
     h = ctypes.c_void_p()

@@ -201,6 +201,22 @@ def test_result_before_run_is_not_ready():
         pm.mertens_destroy(plan)
 
 
+def test_autotune_picks_parameters_that_keep_results():
+    n = 10**12 + 3
+    best, ms = pm.mertens_autotune([n], runs=1)
+    assert ms > 0 and best["u_factor"] > 0 and best["dense_c"] > 0
+    old = pm.mertens_get_tuning()
+    try:
+        ref = gpu_array(n)
+        pm.mertens_set_tuning(**best)
+        got = gpu_array(n)
+        X = len(got[1])
+        assert got[0] == ref[0] == oracle.mertens(n, L=10**8)
+        assert np.array_equal(got[1], oracle.mertens_array(n, X, L=10**8))
+    finally:
+        pm.mertens_set_tuning(**old)
+
+
 # ---- Table 1 values beyond 10^16 ----------------------------------------------
 
 def test_table1_1e18_auto_parameters(table1):
