@@ -407,7 +407,7 @@ def run_native(args, world, rank, local):
 # DRAM bytes (read + write) per launch from one ncu capture of the current
 # kernel (profiles/), or None when the kernel changed since the capture.
 TRAFFIC_PER_LAUNCH = {
-    "mu_sieve": 0.345e6 + 476.590e6,       # profiles/mu_sieve_1e16.md (one 2^28-y block)
+    "mu_sieve": None,                      # kernel changed since the last capture
     "update_dense": 989.370e6 + 5.861e6,   # profiles/dense_update_1e16.md
     "update_gathered": 1670.806e6 + 56.108e6,  # profiles/gather_tile_1e16.md (first block)
 }

@@ -146,9 +146,17 @@ struct mertens_plan_s {
     uint64_t *dJTOP = nullptr, *dJBOT = nullptr, *dS = nullptr, *dR = nullptr;
     uint32_t *dICNT = nullptr, *dIOFF = nullptr, *dScan = nullptr;
     int8_t *dmu_aux = nullptr;
-    int16_t *dMloc = nullptr;
-    int32_t *dsegsum = nullptr;
-    int64_t *dsegoff = nullptr, *dcarry = nullptr;
+    int16_t *dMloc[2] = {nullptr, nullptr};      // sieve output, two blocks in flight
+    int32_t *dsegsum[2] = {nullptr, nullptr};
+    int64_t *dsegoff[2] = {nullptr, nullptr};
+    int64_t *dcarry = nullptr;
+    // streams and events of a run (sieve chain, gathered updates, dense part)
+    bool serial = false;
+    cudaStream_t st_sieve = nullptr, st_upd = nullptr, st_dense = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_reset = nullptr, ev_dense_done = nullptr;
+    cudaEvent_t ev_sieve_done = nullptr, ev_join = nullptr;
+    std::vector<cudaEvent_t> ev_sieved, ev_upd;
+    uint32_t *dcounter_dense = nullptr, *dcounter_gather = nullptr;
     // shared-memory gather path: tiles and items of every block, item range
     // [gblk[b], gblk[b+1]) and last y covered, per block
     GatherTile *dgtiles = nullptr;
@@ -623,15 +631,30 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
     const uint64_t L = block_len;
     const uint64_t nseg = sieve_segments(L);
     p->dmu_aux = p->alloc<int8_t>(p->ydense + 16);
-    p->dMloc = p->alloc<int16_t>(L + 2);
-    p->dsegsum = p->alloc<int32_t>(nseg);
-    p->dsegoff = p->alloc<int64_t>(nseg);
+    // One stream by default: on GB300 the three-stream schedule measured
+    // slower (the sieve and the updates contend for the same SM resources);
+    // MERTENS_OVERLAP=1 selects it.
+    p->serial = getenv("MERTENS_OVERLAP") == nullptr || p->nblocks == 1;
+    const int nbuf = p->serial ? 1 : 2;
+    for (int i = 0; i < 2; ++i) {
+        if (i < nbuf) {
+            p->dMloc[i] = p->alloc<int16_t>(L + 2);
+            p->dsegsum[i] = p->alloc<int32_t>(nseg);
+            p->dsegoff[i] = p->alloc<int64_t>(nseg);
+        } else {
+            p->dMloc[i] = p->dMloc[0];
+            p->dsegsum[i] = p->dsegsum[0];
+            p->dsegoff[i] = p->dsegoff[0];
+        }
+    }
     p->dcarry = p->alloc<int64_t>(p->nblocks + 1);
     p->dgtiles = p->alloc<GatherTile>(gtiles.size() + 1);
     p->dgitems = p->alloc<GatherItem>(gitems.size() + 1);
 
     p->derr = p->alloc<uint32_t>(1);
     p->dcounter = p->alloc<uint32_t>(1);
+    p->dcounter_dense = p->alloc<uint32_t>(1);
+    p->dcounter_gather = p->alloc<uint32_t>(1);
     p->dMG = p->alloc<uint64_t>(p->mg_n + 1);
     p->ddl_m = p->alloc<uint64_t>(nchunks * kChunkCapPad);
     p->ddl_yo = p->alloc<uint16_t>(nchunks * kChunkCapPad);
@@ -644,7 +667,9 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
             rc = MERTENS_ENOMEM;
     bool any_null = !p->dK || !p->dJLO || !p->dJC0 || !p->dJCUR || !p->dYCE || !p->dJTOP ||
                     !p->dJBOT || !p->dS || !p->dR || !p->dICNT || !p->dIOFF || !p->dScan ||
-                    !p->dmu_aux || !p->dMloc || !p->dsegsum || !p->dsegoff || !p->dgtiles ||
+                    !p->dmu_aux || !p->dMloc[0] || !p->dsegsum[0] || !p->dsegoff[0] ||
+                    !p->dMloc[1] || !p->dsegsum[1] || !p->dsegoff[1] || !p->dgtiles ||
+                    !p->dcounter_dense || !p->dcounter_gather ||
                     !p->dgitems || !p->dcarry || !p->derr || !p->dcounter || !p->dMG ||
                     !p->ddl_m || !p->ddl_yo || !p->ddl_cnt || !p->dgroups || !p->ditems ||
                     !p->dqs;
@@ -697,6 +722,24 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
         if (cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming) != cudaSuccess ||
             cudaGetLastError() != cudaSuccess)
             rc = MERTENS_ECUDA;
+        if (rc == MERTENS_OK && !p->serial) {
+            const unsigned fl = cudaEventDisableTiming;
+            bool ok = cudaStreamCreateWithFlags(&p->st_sieve, cudaStreamNonBlocking) == cudaSuccess &&
+                      cudaStreamCreateWithFlags(&p->st_upd, cudaStreamNonBlocking) == cudaSuccess &&
+                      cudaStreamCreateWithFlags(&p->st_dense, cudaStreamNonBlocking) == cudaSuccess &&
+                      cudaEventCreateWithFlags(&p->ev_fork, fl) == cudaSuccess &&
+                      cudaEventCreateWithFlags(&p->ev_reset, fl) == cudaSuccess &&
+                      cudaEventCreateWithFlags(&p->ev_dense_done, fl) == cudaSuccess &&
+                      cudaEventCreateWithFlags(&p->ev_sieve_done, fl) == cudaSuccess &&
+                      cudaEventCreateWithFlags(&p->ev_join, fl) == cudaSuccess;
+            p->ev_sieved.assign(p->nblocks, nullptr);
+            p->ev_upd.assign(p->nblocks, nullptr);
+            for (uint64_t b = 0; ok && b < p->nblocks; ++b)
+                ok = cudaEventCreateWithFlags(&p->ev_sieved[b], fl) == cudaSuccess &&
+                     cudaEventCreateWithFlags(&p->ev_upd[b], fl) == cudaSuccess;
+            if (!ok)
+                rc = MERTENS_ECUDA;
+        }
     }
     if (rc != MERTENS_OK) {
         if (rc == MERTENS_ENOMEM)
@@ -781,34 +824,59 @@ static void clear_events(mertens_plan_s *p)
     p->prof_runs = 0;
 }
 
-// Enqueues one whole run (all blocks, then resolve) on s; *out = kernels.
-static int run_enqueue(mertens_plan_s *p, cudaStream_t s, uint64_t *out)
+// Enqueues one whole run (all blocks, then resolve) forked from stream
+// `origin` onto three streams and joined back: the sieve chain (block by
+// block, two output buffers), the per-block gathered updates (each after its
+// block's sieve; the sieve of block b+2 waits for them, as it reuses the
+// buffer), and the dense update (after the block that completes the
+// squarefree list).  S only receives commutative atomic additions, so the
+// dense and gathered updates may interleave.  *out = kernels launched.
+static int run_enqueue(mertens_plan_s *p, cudaStream_t origin, uint64_t *out)
 {
     uint64_t launches = 0;
     int r;
     const size_t E = p->nent;
-    cudaMemsetAsync(p->dS, 0, E * 8, s);
-    cudaMemcpyAsync(p->dJCUR, p->dJC0, E * 8, cudaMemcpyDeviceToDevice, s);
-    cudaMemsetAsync(p->dcarry, 0, 8 * (p->nblocks + 1), s);
-    cudaMemsetAsync(p->derr, 0, 4, s);
+    const bool serial = p->serial;
+    cudaStream_t ss = serial ? origin : p->st_sieve;
+    cudaStream_t su = serial ? origin : p->st_upd;
+    cudaStream_t sd = serial ? origin : p->st_dense;
+    if (!serial) {
+        cudaEventRecord(p->ev_fork, origin);
+        cudaStreamWaitEvent(ss, p->ev_fork, 0);
+        cudaStreamWaitEvent(su, p->ev_fork, 0);
+        cudaStreamWaitEvent(sd, p->ev_fork, 0);
+    }
+    cudaMemsetAsync(p->dS, 0, E * 8, su);
+    cudaMemcpyAsync(p->dJCUR, p->dJC0, E * 8, cudaMemcpyDeviceToDevice, su);
+    cudaMemsetAsync(p->dcarry, 0, 8 * (p->nblocks + 1), ss);
+    cudaMemsetAsync(p->derr, 0, 4, su);
     if (!p->mg_built) {
-        r = magic_table_enqueue(p->dMG, p->mg_n, s);
+        r = magic_table_enqueue(p->dMG, p->mg_n, su);
         if (r < 0)
             goto fail;
         launches += r;
         p->mg_built = true;
+    }
+    if (!serial) {
+        // the dense update needs S cleared and the divisor magics
+        cudaEventRecord(p->ev_reset, su);
+        cudaStreamWaitEvent(sd, p->ev_reset, 0);
     }
     {
         bool dense_done = false;
         for (uint64_t b = 0; b < p->nblocks; ++b) {
             const uint64_t y1 = 1 + b * p->block_len;
             const uint64_t y2 = std::min(y1 + p->block_len - 1, p->y_max);
+            const int buf = (int)(b & 1);
+            if (!serial && b >= 2)
+                cudaStreamWaitEvent(ss, p->ev_upd[b - 2], 0);
+            cudaStream_t s = ss;
             SieveLaunch L;
             L.y1 = y1;
             L.len = y2 - y1 + 1;
-            L.Mloc = p->dMloc;
-            L.segsum = p->dsegsum;
-            L.segoff = p->dsegoff;
+            L.Mloc = p->dMloc[buf];
+            L.segsum = p->dsegsum[buf];
+            L.segoff = p->dsegoff[buf];
             L.carry_in = p->dcarry + b;
             L.carry_out = p->dcarry + b + 1;
             L.mu_out = (y1 <= p->ydense) ? p->dmu_aux : nullptr;
@@ -832,7 +900,12 @@ static int run_enqueue(mertens_plan_s *p, cudaStream_t s, uint64_t *out)
             if (r < 0)
                 goto fail;
             launches += r;
+            if (!serial)
+                cudaEventRecord(p->ev_sieved[b], ss);
             if (!dense_done && y2 >= p->ydense) {
+                s = sd;
+                if (!serial)
+                    cudaStreamWaitEvent(sd, p->ev_sieved[b], 0);
                 ev_begin(p, kPhDense, s, &pe);
                 r = dense_list_enqueue(p->dmu_aux, p->ydense, p->dMG, p->ddl_m, p->ddl_yo,
                                        p->ddl_cnt, s);
@@ -842,7 +915,7 @@ static int run_enqueue(mertens_plan_s *p, cudaStream_t s, uint64_t *out)
                 DenseArgs da;
                 da.items = p->ditems;
                 da.nitems = p->nitems;
-                da.counter = p->dcounter;
+                da.counter = p->dcounter_dense;
                 da.groups = p->dgroups;
                 da.K = p->dK;
                 da.YCE = p->dYCE;
@@ -850,6 +923,7 @@ static int run_enqueue(mertens_plan_s *p, cudaStream_t s, uint64_t *out)
                 da.dl_yo = p->ddl_yo;
                 da.dl_cnt = p->ddl_cnt;
                 da.S = p->dS;
+                da.ctas_per_sm = serial ? 0 : 1;
                 r = dense_update_enqueue(da, s);
                 ev_end(p, s, &pe);
                 if (r < 0)
@@ -857,6 +931,9 @@ static int run_enqueue(mertens_plan_s *p, cudaStream_t s, uint64_t *out)
                 launches += r;
                 dense_done = true;
             }
+            s = su;
+            if (!serial)
+                cudaStreamWaitEvent(su, p->ev_sieved[b], 0);
             SparseBlockArgs sb;
             sb.y1 = y1;
             sb.y2 = y2;
@@ -877,8 +954,8 @@ static int run_enqueue(mertens_plan_s *p, cudaStream_t s, uint64_t *out)
             sa.S = p->dS;
             sa.ICNT = p->dICNT;
             sa.IOFF = p->dIOFF;
-            sa.Mloc = p->dMloc;
-            sa.segoff = p->dsegoff;
+            sa.Mloc = p->dMloc[buf];
+            sa.segoff = p->dsegoff[buf];
             sa.y_lo = p->gend[b] + 1 > y1 ? p->gend[b] + 1 : y1;
             sa.m_ylo = magic_of(sa.y_lo);
             sa.l_ylo = magic_shift(sa.y_lo);
@@ -888,9 +965,11 @@ static int run_enqueue(mertens_plan_s *p, cudaStream_t s, uint64_t *out)
                 ga.tiles = p->dgtiles;
                 ga.items = p->dgitems + p->gblk[b];
                 ga.nitems = p->gblk[b + 1] - p->gblk[b];
-                ga.counter = p->dcounter;
-                ga.Mloc = p->dMloc;
-                ga.segoff = p->dsegoff;
+                ga.counter = p->dcounter_gather;
+                ga.Mloc = p->dMloc[buf];
+                ga.segoff = p->dsegoff[buf];
+                ga.threads = serial ? 512 : 256;
+                ga.ctas_per_sm = serial ? 0 : 2;
                 ga.K = p->dK;
                 ga.JLO = p->dJLO;
                 ga.JCUR = p->dJCUR;
@@ -909,14 +988,27 @@ static int run_enqueue(mertens_plan_s *p, cudaStream_t s, uint64_t *out)
             if (r < 0)
                 goto fail;
             launches += r;
+            if (!serial)
+                cudaEventRecord(p->ev_upd[b], su);
+        }
+        if (!serial) {
+            // resolve after every update; join all streams back to origin
+            cudaEventRecord(p->ev_dense_done, sd);
+            cudaStreamWaitEvent(su, p->ev_dense_done, 0);
+            cudaEventRecord(p->ev_sieve_done, ss);
+            cudaStreamWaitEvent(su, p->ev_sieve_done, 0);
         }
         PhaseEvents pe;
-        ev_begin(p, kPhResolve, s, &pe);
-        r = resolve_enqueue(p->dqs, (uint32_t)p->nq, p->dS, p->dK, p->dR, s);
-        ev_end(p, s, &pe);
+        ev_begin(p, kPhResolve, su, &pe);
+        r = resolve_enqueue(p->dqs, (uint32_t)p->nq, p->dS, p->dK, p->dR, su);
+        ev_end(p, su, &pe);
         if (r < 0)
             goto fail;
         launches += r;
+        if (!serial) {
+            cudaEventRecord(p->ev_join, su);
+            cudaStreamWaitEvent(origin, p->ev_join, 0);
+        }
     }
     *out = launches;
     return MERTENS_OK;
@@ -1047,6 +1139,18 @@ void mertens_destroy(mertens_plan_t p)
         cudaGraphExecDestroy(p->gexec);
     if (p->cap_stream)
         cudaStreamDestroy(p->cap_stream);
+    for (cudaStream_t s : {p->st_sieve, p->st_upd, p->st_dense})
+        if (s)
+            cudaStreamDestroy(s);
+    for (cudaEvent_t e : {p->ev_fork, p->ev_reset, p->ev_dense_done, p->ev_sieve_done, p->ev_join})
+        if (e)
+            cudaEventDestroy(e);
+    for (cudaEvent_t e : p->ev_sieved)
+        if (e)
+            cudaEventDestroy(e);
+    for (cudaEvent_t e : p->ev_upd)
+        if (e)
+            cudaEventDestroy(e);
     if (p->pt.np)
         prime_table_destroy(&p->pt);
     for (auto &a : p->allocs)

@@ -93,22 +93,13 @@ __device__ __forceinline__ void sieve_prime_warp(const SieveArgs &a, uint32_t *w
         c = (uint32_t)(cs - div_magic(cs << 1, m, l) * p);
     }
     const uint32_t add = a.lg[t] | kCountOne;
-    // (c + lane) mod p and 32 mod p with p >= 11: at most three subtractions
-    uint32_t ci = c + (uint32_t)lane;
-    while (ci >= p)
-        ci -= p;
-    uint32_t inc = 32u;
-    while (inc >= p)
-        inc -= p;
-    for (uint32_t yo = off + (uint32_t)lane * p; yo < hi; yo += 32u * p) {
-        const uint32_t sh = (yo & 1u) << 4;
-        atomicAdd(&w[yo >> 1], add << sh);
-        if (ci == 0)
-            atomicOr(&w[yo >> 1], kSquareBit << sh);
-        ci += inc;
-        if (ci >= p)
-            ci -= p;
-    }
+    for (uint32_t yo = off + (uint32_t)lane * p; yo < hi; yo += 32u * p)
+        atomicAdd(&w[yo >> 1], add << ((yo & 1u) << 4));
+    // multiples of p^2: the first is (c ? p - c : 0) multiples of p after off
+    // (p < 2048, so p^2 and these offsets fit 32 bits)
+    const uint32_t p2 = p * p;
+    for (uint32_t yo = off + (c ? p - c : 0u) * p + (uint32_t)lane * p2; yo < hi; yo += 32u * p2)
+        atomicOr(&w[yo >> 1], kSquareBit << ((yo & 1u) << 4));
 }
 
 // One tile of kSieveTile y.  Shared half-word per y: every sieving prime p
@@ -181,13 +172,13 @@ __global__ void __launch_bounds__(kSieveThreads, 1) mu_sieve_kernel(SieveArgs a)
                 unsigned l;
                 first_multiple(a, t, a0, p, off, c, m, l);
                 const uint32_t add = a.lg[t] | kCountOne;
-                for (uint32_t yo = off; yo < tl; yo += p) {
-                    const uint32_t sh = (yo & 1u) << 4;
-                    atomicAdd(&w[yo >> 1], add << sh);
-                    if (c == 0)
-                        atomicOr(&w[yo >> 1], kSquareBit << sh);
-                    c = (c + 1 == p) ? 0u : c + 1;
-                }
+                for (uint32_t yo = off; yo < tl; yo += p)
+                    atomicAdd(&w[yo >> 1], add << ((yo & 1u) << 4));
+                // p^2 > 2^22 > tile: at most one multiple of p^2, (c ? p - c : 0)
+                // multiples of p after off
+                const uint64_t sq = (uint64_t)off + (uint64_t)(c ? p - c : 0u) * p;
+                if (sq < tl)
+                    atomicOr(&w[sq >> 1], kSquareBit << (((uint32_t)sq & 1u) << 4));
             }
         }
     }

@@ -517,6 +517,8 @@ int dense_update_enqueue(const DenseArgs &a, cudaStream_t s)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, dense_update_kernel, kDenseThreads, smem);
     if (per < 1)
         per = 1;
+    if (a.ctas_per_sm && (int)a.ctas_per_sm < per)
+        per = (int)a.ctas_per_sm;
     uint32_t grid = (uint32_t)(sms * per);
     if (grid > a.nitems)
         grid = a.nitems;
@@ -557,14 +559,17 @@ int gather_tiles_enqueue(const GatherArgs &a, cudaStream_t s)
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, gather_tile_kernel, 512, smem);
+    const int threads = a.threads == 256 ? 256 : 512;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, gather_tile_kernel, threads, smem);
     if (per < 1)
         per = 1;
+    if (a.ctas_per_sm && (int)a.ctas_per_sm < per)
+        per = (int)a.ctas_per_sm;
     uint32_t grid = (uint32_t)(sms * per);
     if (grid > a.nitems)
         grid = a.nitems;
     cudaMemsetAsync(a.counter, 0, 4, s);
-    gather_tile_kernel<<<grid, 512, smem, s>>>(a);
+    gather_tile_kernel<<<grid, threads, smem, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 

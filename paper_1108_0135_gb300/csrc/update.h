@@ -40,6 +40,7 @@ struct DenseArgs {
     const uint16_t *dl_yo;
     const uint32_t *dl_cnt;
     uint64_t *S;
+    uint32_t ctas_per_sm;  // 0: as many as fit; else at most this many per SM
 };
 
 // Invariant-divisor constants of one block [y1, y2].
@@ -92,6 +93,8 @@ struct GatherArgs {
     const int64_t *segoff;
     const uint64_t *K, *JLO, *JCUR, *MG;
     uint64_t *S;
+    uint32_t threads;      // 256 or 512 per CTA
+    uint32_t ctas_per_sm;  // 0: as many as fit; else at most this many per SM
 };
 
 int magic_table_enqueue(uint64_t *MG, uint64_t nd, cudaStream_t s);
