@@ -37,6 +37,25 @@ constexpr uint32_t kSquareBit = 1u << 15;
 constexpr uint32_t kPatternPeriod = 44100;
 constexpr uint32_t kPatternWords = kPatternPeriod / 2;
 
+// Byte sieve (the fast variant of a1 + a2): one byte per y holding the sum of
+// odd weights w(p) = the odd integer nearest 4 log2 p (so its parity is the
+// parity of the prime count), and one bit per y set when a prime square
+// divides y.  A tile of kByteTile y takes 128 KiB + 16 KiB of shared memory.
+constexpr int kByteTile = 131072;
+constexpr int kByteWords = kByteTile / 4;
+constexpr int kByteSqWords = kByteTile / 32;
+constexpr int kByteScale = 4;
+// Pre-sieve tables of the byte sieve: 16 copies of the byte pattern of
+// 2, 3, 5, 7, copy k starting at phase k, each long enough for any phase plus
+// one tile (so a tile is one 16-byte aligned copy), and the square flags of
+// 4, 9, 25, 49 as one long bit string read with a funnel shift.
+constexpr uint32_t kPat8Len = 175184;   // >= 44100 + 131072, multiple of 16
+constexpr uint32_t kPatSqWords = 5480;  // > (44100 + 131072 + 64) / 32
+// Tiles whose first y is at least this take one decision threshold for the
+// whole tile (4 log2 y moves by < 0.012 over a tile); lower tiles decide
+// with a threshold per y.
+constexpr uint64_t kByteTileThrMin = 1ull << 26;
+
 // Error bits of the plan's device status word.
 constexpr uint32_t kErrMOverflow = 1u;   // |M(y)| did not fit int32
 constexpr uint32_t kErrBadIndex = 2u;    // a self-check found an index out of range
@@ -85,6 +104,21 @@ __host__ __device__ inline uint64_t magic_of(uint64_t d)
 __device__ __forceinline__ uint64_t div_magic(uint64_t k2, uint64_t m, unsigned l)
 {
     return __umul64hi(k2, m) >> l;
+}
+
+// The same theorem with 31-bit numerators: for 2 <= d < 2^31, l = ceil(log2 d)
+// and m = floor(2^(31+l)/d) + 1 < 2^32, every v < 2^31 has
+// floor(v/d) = floor(mulhi32(m, v) / 2^(l-1)).  Returns m; *s = l - 1.
+__host__ __device__ inline uint32_t magic32_of(uint32_t d, unsigned *s)
+{
+    const unsigned l = bitlen64((uint64_t)d - 1);
+    *s = l - 1;
+    return (uint32_t)(((1ull << (31 + l)) / d) + 1ull);
+}
+
+__device__ __forceinline__ uint32_t div_magic32(uint32_t v, uint32_t m, unsigned s)
+{
+    return __umulhi(v, m) >> s;
 }
 
 // Warp-wide sum of a 64-bit value (mod 2^64).

@@ -32,6 +32,11 @@ struct PrimeTable {
     uint32_t *blk_qm = nullptr;   // per block: floor(y1 / p) mod p
     uint32_t *pat_even = nullptr; // pre-sieve pattern words for an even phase
     uint32_t *pat_odd = nullptr;  // ... and for an odd phase
+    // byte sieve (null when the table was built without it)
+    uint4 *pq = nullptr;          // {p, m32(p), m32(p^2) or 0, s(p) | s(p^2) << 8 | w(p) << 16}
+    uint64_t *blk_r2 = nullptr;   // per block: y1 mod p^2
+    uint4 *pat8 = nullptr;        // 16 phase copies of the byte pattern
+    uint32_t *patsq = nullptr;    // square flags of 4, 9, 25, 49 as a long bit string
     // host copy of the primes (for counting primes <= a bound)
     uint32_t *host_p = nullptr;
     Allocator al;
@@ -53,8 +58,10 @@ struct SieveLaunch {
     cudaEvent_t mid2 = nullptr;  // ... and this one before a2 (profiling)
 };
 
-// Builds the prime table for sieving up to y_max (host + device upload).
-int prime_table_create(PrimeTable *t, const Allocator &al, uint64_t y_max, cudaStream_t s);
+// Builds the prime table for sieving up to y_max (host + device upload);
+// with_bytes adds the tables of the byte sieve.
+int prime_table_create(PrimeTable *t, const Allocator &al, uint64_t y_max, cudaStream_t s,
+                       bool with_bytes = true);
 void prime_table_destroy(PrimeTable *t);
 // Number of primes in the table that are <= b.
 uint32_t prime_count_upto(const PrimeTable *t, uint64_t b);

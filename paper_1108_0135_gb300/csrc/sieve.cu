@@ -6,6 +6,7 @@
 // M(y1 - 1) from the previous block.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -18,7 +19,8 @@ namespace mert {
 // a1: per-block remainders of the sieving primes.
 // ---------------------------------------------------------------------------
 __global__ void sieve_block_prep_kernel(uint64_t y1, uint32_t np, const uint32_t *__restrict__ p,
-                                        uint32_t *__restrict__ r, uint32_t *__restrict__ qm)
+                                        uint32_t *__restrict__ r, uint32_t *__restrict__ qm,
+                                        uint64_t *__restrict__ r2)
 {
     uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= np)
@@ -26,6 +28,8 @@ __global__ void sieve_block_prep_kernel(uint64_t y1, uint32_t np, const uint32_t
     uint64_t pp = p[t];
     r[t] = (uint32_t)(y1 % pp);
     qm[t] = (uint32_t)((y1 / pp) % pp);
+    if (r2)
+        r2[t] = y1 % (pp * pp);
 }
 
 struct SieveArgs {
@@ -273,6 +277,256 @@ __global__ void __launch_bounds__(kSieveThreads, 1) mu_sieve_kernel(SieveArgs a)
         a.segsum[(a0 + so) >> kSegShift] = run;
 }
 
+// ---------------------------------------------------------------------------
+// a1 + a2, byte variant.  Same method (Sec. 3 log sieve, then the prefix sum),
+// laid out for issue throughput: one byte per y and one square bit per y, so a
+// tile holds 131072 y; every division of the per-tile set-up is a 32-bit
+// invariant-divisor multiply; and the decode works on four y per 32-bit word.
+//
+// Byte of y: B0 + sum over the distinct sieving primes p | y of w(p), where
+// w(p) is the odd integer nearest 4 log2 p (|w(p) - 4 log2 p| <= 1) and B0 a
+// bias fixed per tile.  Because every weight is odd, the parity of the sum is
+// the parity of the prime count.  For squarefree y with unsieved cofactor c
+// (1 or a prime > P, as in the 16-bit kernel) the weight sum A satisfies
+//     c = 1:  A >= 4 log2 y - E,     c > 1:  A <= 4 log2 y - 4 log2 P + E,
+// E <= 11 the summed rounding error (y < 2^42 has at most 11 distinct prime
+// factors).  With P >= 2^10 the threshold T = 4 log2 y - 2 log2 P separates
+// the two with >= 9 units either side, so an integer threshold anywhere in
+// [T - 2, T] is exact; tiles at y >= 2^26 use one even threshold thr per tile
+// and B0 = 127 - thr (odd), which puts the decision into bit 7 of the byte
+// and the count parity (xor 1) into bit 0:  mu = -1 exactly when bit 0 and
+// bit 7 of the biased byte differ.  Bytes stay below 2^8 (A + B0 <= 182).
+// ---------------------------------------------------------------------------
+struct ByteArgs {
+    uint64_t y1;
+    uint32_t len;         // <= 2^30
+    uint32_t np;          // primes used (all p <= P)
+    uint32_t np_piece;    // [4, np_piece): p < 128, sieved in eighth-tile pieces
+    uint32_t np_small;    // [np_piece, np_small): p < 2048, a warp per prime
+    float thr_half;       // 2 log2 P
+    const uint4 *pq;
+    const uint32_t *r;    // y1 mod p
+    const uint64_t *r2;   // y1 mod p^2
+    const uint4 *pat8;
+    const uint32_t *patsq;
+    int16_t *Mloc;
+    int32_t *segsum;
+    int8_t *mu_out;
+    uint64_t mu_base, mu_end;
+};
+
+// Multiples of a prime p < 2048 in the tile offsets [lo, hi), lanes over them.
+// The step 32p is a multiple of 4, so each lane stays on one byte of the word
+// and its shifted weight is loop-invariant.
+__device__ __forceinline__ void byte_prime_warp(const ByteArgs &a, uint32_t *w, uint32_t *sq,
+                                                uint32_t t, uint32_t a0, uint32_t lo, uint32_t hi,
+                                                uint32_t lane)
+{
+    const uint4 q = a.pq[t];
+    const uint32_t p = q.x;
+    const uint32_t v = a.r[t] + a0 + lo;  // < 2^31
+    const uint32_t rem = v - div_magic32(v, q.y, q.w & 255u) * p;
+    const uint32_t yo = lo + (rem ? p - rem : 0u) + lane * p;
+    const uint32_t wsh = (q.w >> 16) << ((yo & 3u) << 3);
+    const uint32_t step = 8u * p;  // words per 32 multiples
+    const uint32_t end = (hi + 3u - (yo & 3u)) >> 2;  // yo' < hi  <=>  yo' >> 2 < end
+#pragma unroll 4
+    for (uint32_t wi = yo >> 2; wi < end; wi += step)
+        atomicAdd(&w[wi], wsh);
+    const uint32_t p2 = p * p;
+    const uint32_t v2 = (uint32_t)a.r2[t] + a0 + lo;  // < 2^31
+    const uint32_t rem2 = v2 - div_magic32(v2, q.z, (q.w >> 8) & 255u) * p2;
+    for (uint32_t y2o = lo + (rem2 ? p2 - rem2 : 0u) + lane * p2; y2o < hi; y2o += 32u * p2)
+        atomicOr(&sq[y2o >> 5], 1u << (y2o & 31u));
+}
+
+// One prime p >= 2048 per lane over the whole tile; p^2 > tile, so at most
+// one multiple of p^2.
+__device__ __forceinline__ void byte_prime_lane(const ByteArgs &a, uint32_t *w, uint32_t *sq,
+                                                uint32_t t, uint32_t a0, uint32_t tl)
+{
+    const uint4 q = a.pq[t];
+    const uint32_t p = q.x;
+    const uint32_t wt = q.w >> 16;
+    const uint32_t v = a.r[t] + a0;  // < 2^31
+    const uint32_t rem = v - div_magic32(v, q.y, q.w & 255u) * p;
+    for (uint32_t yo = rem ? p - rem : 0u; yo < tl; yo += p)
+        atomicAdd(&w[yo >> 2], __funnelshift_l(0u, wt, yo << 3));
+    uint64_t o2;
+    if (q.z) {  // p^2 < 2^30: 32-bit division
+        const uint32_t p2 = p * p;
+        const uint32_t v2 = (uint32_t)a.r2[t] + a0;  // < 2^31
+        const uint32_t rem2 = v2 - div_magic32(v2, q.z, (q.w >> 8) & 255u) * p2;
+        o2 = rem2 ? p2 - rem2 : 0u;
+    } else {  // p^2 >= 2^30 > a0: y1 mod p^2 + a0 < 2 p^2
+        const uint64_t p2 = (uint64_t)p * p;
+        uint64_t v2 = a.r2[t] + a0;
+        if (v2 >= p2)
+            v2 -= p2;
+        o2 = v2 ? p2 - v2 : 0u;
+    }
+    if (o2 < tl)
+        atomicOr(&sq[(uint32_t)o2 >> 5], 1u << ((uint32_t)o2 & 31u));
+}
+
+// floor(4 log2 y - 2 log2 P) for one y (tiles below 2^26).
+__device__ __forceinline__ int byte_thr(uint64_t y, float thr_half)
+{
+    return (int)floorf((float)kByteScale * __log2f(__ull2float_rn(y)) - thr_half);
+}
+
+__global__ void __launch_bounds__(kSieveThreads, 1) mu_sieve_byte_kernel(ByteArgs a)
+{
+    extern __shared__ uint4 sb[];
+    uint32_t *w = reinterpret_cast<uint32_t *>(sb);  // kByteWords words, four y each
+    uint32_t *sq = w + kByteWords;                     // kByteSqWords words, 32 y each
+    __shared__ uint32_t s_job;
+    const uint32_t a0 = blockIdx.x * (uint32_t)kByteTile;
+    const uint64_t t1 = a.y1 + a0;
+    const uint32_t tl = min(a.len - a0, (uint32_t)kByteTile);
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+
+    // pre-sieve pattern: bytes of 2, 3, 5, 7 and square flags of 4, 9, 25, 49
+    {
+        const uint32_t ph = (uint32_t)(t1 % kPatternPeriod);
+        const uint4 *src = a.pat8 + (size_t)(ph & 15u) * (kPat8Len / 16) + (ph >> 4);
+#pragma unroll 4
+        for (uint32_t i = threadIdx.x; i < (uint32_t)kByteTile / 16; i += kSieveThreads)
+            sb[i] = src[i];
+        const uint32_t j0 = ph >> 5, s = ph & 31u;
+        for (uint32_t i = threadIdx.x; i < (uint32_t)kByteSqWords; i += kSieveThreads)
+            sq[i] = __funnelshift_r(a.patsq[j0 + i], a.patsq[j0 + i + 1], s);
+        if (threadIdx.x == 0)
+            s_job = 0;
+    }
+    __syncthreads();
+
+    const uint32_t jp = a.np_piece > 4 ? 8u * (a.np_piece - 4) : 0u;
+    const uint32_t js = jp + (a.np_small - a.np_piece);
+    const uint32_t jobs = js + (a.np - a.np_small + 31u) / 32u;
+    for (;;) {
+        uint32_t job = 0;
+        if (lane == 0)
+            job = atomicAdd(&s_job, 1u);
+        job = __shfl_sync(0xffffffffu, job, 0);
+        if (job >= jobs)
+            break;
+        if (job < jp) {
+            const uint32_t k = job & 7u;
+            const uint32_t lo = k * (kByteTile / 8), hi = min(tl, (k + 1) * (kByteTile / 8));
+            if (lo < hi)
+                byte_prime_warp(a, w, sq, 4 + (job >> 3), a0, lo, hi, lane);
+        } else if (job < js) {
+            byte_prime_warp(a, w, sq, a.np_piece + (job - jp), a0, 0, tl, lane);
+        } else {
+            const uint32_t t = a.np_small + (job - js) * 32u + lane;
+            if (t < a.np)
+                byte_prime_lane(a, w, sq, t, a0, tl);
+        }
+    }
+    __syncthreads();
+
+    // decode + scan: warp owns two segments, 16 y per lane per round
+    const bool tile_thr = t1 >= kByteTileThrMin;
+    uint32_t bias4 = 0;
+    if (tile_thr) {
+        int thr = (int)floorf((float)kByteScale * log2f(__ull2float_rn(t1)) - a.thr_half);
+        thr &= ~1;
+        bias4 = (uint32_t)(127 - thr) * 0x01010101u;
+    }
+    for (uint32_t sgi = 0; sgi < 2; ++sgi) {
+        const uint32_t so = warp * (2u * kSegY) + sgi * kSegY;  // segment start in the tile
+        if (so >= tl)
+            break;
+        const uint64_t ys = t1 + so;
+        const bool want_mu = a.mu_out && ys <= a.mu_end && ys + (kSegY - 1) >= a.mu_base;
+        int run = 0;
+#pragma unroll 1
+        for (uint32_t r = 0; r < (uint32_t)kSegY / 512u; ++r) {
+            const uint32_t o0 = so + r * 512u + lane * 16u;  // first of the lane's 16 y
+            const uint4 q4 = sb[o0 >> 4];
+            const uint32_t sqw = sq[o0 >> 5] >> (o0 & 16u);
+            const uint32_t ws[4] = {q4.x, q4.y, q4.z, q4.w};
+            uint32_t D[4], pbs[4], mbs[4];
+            int tot = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                // square flag of byte j at bit 8j
+                const uint32_t sqb = ((sqw >> (4 * k)) & 15u) * 0x00204081u;
+                uint32_t neg;
+                if (tile_thr) {
+                    const uint32_t W = ws[k] + bias4;
+                    neg = (W ^ (W >> 7)) & 0x01010101u;
+                } else {
+                    neg = 0;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const uint32_t A = (ws[k] >> (8 * j)) & 255u;
+                        const int th = byte_thr(t1 + o0 + 4 * k + j, a.thr_half);
+                        // count parity xor [c > 1]
+                        const uint32_t bit = (A & 1u) ^ ((int)A > th ? 0u : 1u);
+                        neg |= bit << (8 * j);
+                    }
+                }
+                uint32_t pb = ~sqb & ~neg & 0x01010101u;  // mu = +1
+                uint32_t mb = ~sqb & neg;                 // mu = -1
+                if (o0 + 4u * k + 4u > tl) {
+                    const uint32_t keep = o0 + 4u * k >= tl ? 0u
+                                          : 0xffffffffu >> (8u * (o0 + 4u * k + 4u - tl));
+                    pb &= keep;
+                    mb &= keep;
+                }
+                pbs[k] = pb;
+                mbs[k] = mb;
+                // byte j: 4 + sum of mu over bytes 0..j, in [0, 8]
+                D[k] = (pb - mb + 0x01010101u) * 0x01010101u + 0x00010203u;
+                tot += (int)(D[k] >> 24) - 4;
+            }
+            int inc = tot;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int nb = __shfl_up_sync(0xffffffffu, inc, o);
+                if ((int)lane >= o)
+                    inc += nb;
+            }
+            int rb = run + inc - tot;  // M relative to the segment, before the lane's 16 y
+            run += __shfl_sync(0xffffffffu, inc, 31);
+            uint32_t out[8];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                // halfword = 0x8000 + value, so no borrow crosses halves; the
+                // xor turns 0x8000 + v into v mod 2^16
+                const uint32_t bx = (uint32_t)(rb - 4) * 0x00010001u;
+                out[2 * k] = (bx + __byte_perm(D[k], 0x80u, 0x4140)) ^ 0x80008000u;
+                out[2 * k + 1] = (bx + __byte_perm(D[k], 0x80u, 0x4342)) ^ 0x80008000u;
+                rb += (int)(D[k] >> 24) - 4;
+            }
+            int16_t *dst = a.Mloc + a0 + o0;
+            if (o0 + 16u <= tl) {
+                reinterpret_cast<uint4 *>(dst)[0] = make_uint4(out[0], out[1], out[2], out[3]);
+                reinterpret_cast<uint4 *>(dst)[1] = make_uint4(out[4], out[5], out[6], out[7]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 16; ++k)
+                    if (o0 + k < tl)
+                        dst[k] = (int16_t)(out[k >> 1] >> (16 * (k & 1)));
+            }
+            if (want_mu) {
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    const uint64_t y = t1 + o0 + k;
+                    const uint32_t sh = 8u * (k & 3);
+                    const int mu = (int)((pbs[k >> 2] >> sh) & 1u) - (int)((mbs[k >> 2] >> sh) & 1u);
+                    if (o0 + k < tl && y >= a.mu_base && y <= a.mu_end)
+                        a.mu_out[y - a.mu_base] = (int8_t)mu;
+                }
+            }
+        }
+        if (lane == 0)
+            a.segsum[(a0 + so) >> kSegShift] = run;
+    }
+}
+
 // a2 finish: segoff[s] = carry_in + sum of segsum[0..s) (int64), and
 // carry_out = carry_in + all of them.  Each CTA scans 1024 segments and adds
 // the sum of all segments before its range.
@@ -339,7 +593,67 @@ static uint64_t isqrt_u64(uint64_t v)
     return r;
 }
 
-int prime_table_create(PrimeTable *t, const Allocator &al, uint64_t y_max, cudaStream_t s)
+// Odd integer nearest kByteScale * log2 p (ties upward).
+static uint32_t byte_weight(uint32_t p)
+{
+    const double x = kByteScale * std::log2((double)p);
+    return 2u * (uint32_t)std::floor((x - 1.0) / 2.0 + 0.5) + 1u;
+}
+
+// Tables of the byte sieve (see mu_sieve_byte_kernel).
+static int byte_tables_create(PrimeTable *t, const std::vector<uint32_t> &pr, cudaStream_t s)
+{
+    const size_t np = pr.size();
+    std::vector<uint4> pq(np);
+    for (size_t i = 0; i < np; ++i) {
+        const uint32_t p = pr[i];
+        unsigned s1 = 0, s2 = 0;
+        const uint32_t m1 = magic32_of(p, &s1);
+        const uint64_t p2 = (uint64_t)p * p;
+        const uint32_t m2 = p2 < (1ull << 30) ? magic32_of((uint32_t)p2, &s2) : 0u;
+        pq[i] = make_uint4(p, m1, m2, s1 | (s2 << 8) | (byte_weight(p) << 16));
+    }
+    uint32_t w[4];
+    const uint32_t small[4] = {2, 3, 5, 7};
+    for (int q = 0; q < 4; ++q)
+        w[q] = byte_weight(small[q]);
+    std::vector<uint8_t> pat(kPatternPeriod);
+    std::vector<uint8_t> sqp(kPatternPeriod);
+    for (uint32_t i = 0; i < kPatternPeriod; ++i) {
+        uint32_t b = 0, f = 0;
+        for (int q = 0; q < 4; ++q) {
+            if (i % small[q] == 0)
+                b += w[q];
+            if (i % (small[q] * small[q]) == 0)
+                f = 1;
+        }
+        pat[i] = (uint8_t)b;
+        sqp[i] = (uint8_t)f;
+    }
+    std::vector<uint8_t> p8((size_t)16 * kPat8Len);
+    for (uint32_t k = 0; k < 16; ++k)
+        for (uint32_t j = 0; j < kPat8Len; ++j)
+            p8[(size_t)k * kPat8Len + j] = pat[(k + j) % kPatternPeriod];
+    std::vector<uint32_t> psq(kPatSqWords, 0u);
+    for (uint32_t j = 0; j < 32u * kPatSqWords; ++j)
+        if (sqp[j % kPatternPeriod])
+            psq[j >> 5] |= 1u << (j & 31u);
+    t->pq = (uint4 *)dev_alloc(t->al, np * sizeof(uint4));
+    t->blk_r2 = (uint64_t *)dev_alloc(t->al, np * 8);
+    t->pat8 = (uint4 *)dev_alloc(t->al, p8.size());
+    t->patsq = (uint32_t *)dev_alloc(t->al, kPatSqWords * 4);
+    if (!t->pq || !t->blk_r2 || !t->pat8 || !t->patsq)
+        return 2;
+    cudaMemcpyAsync(t->pq, pq.data(), np * sizeof(uint4), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(t->pat8, p8.data(), p8.size(), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(t->patsq, psq.data(), kPatSqWords * 4, cudaMemcpyHostToDevice, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess)
+        return 3;
+    return 0;
+}
+
+int prime_table_create(PrimeTable *t, const Allocator &al, uint64_t y_max, cudaStream_t s,
+                       bool with_bytes)
 {
     t->al = al;
     uint64_t B = isqrt_u64(y_max);
@@ -400,6 +714,8 @@ int prime_table_create(PrimeTable *t, const Allocator &al, uint64_t y_max, cudaS
     cudaMemcpyAsync(t->pat_odd, po.data(), kPatternWords * 4, cudaMemcpyHostToDevice, s);
     if (cudaStreamSynchronize(s) != cudaSuccess)
         return 3;
+    if (with_bytes)
+        return byte_tables_create(t, pr, s);
     return 0;
 }
 
@@ -414,6 +730,10 @@ void prime_table_destroy(PrimeTable *t)
     dev_free(t->al, t->blk_qm, np * 4);
     dev_free(t->al, t->pat_even, kPatternWords * 4);
     dev_free(t->al, t->pat_odd, kPatternWords * 4);
+    dev_free(t->al, t->pq, np * sizeof(uint4));
+    dev_free(t->al, t->blk_r2, np * 8);
+    dev_free(t->al, t->pat8, (size_t)16 * kPat8Len);
+    dev_free(t->al, t->patsq, kPatSqWords * 4);
     free(t->host_p);
     *t = PrimeTable();
 }
@@ -431,12 +751,26 @@ uint32_t prime_count_upto(const PrimeTable *t, uint64_t b)
     return lo;
 }
 
+// The byte kernel is exact when all primes up to P >= 2^10 are sieved, y stays
+// below 2^42 (at most 11 distinct prime factors, bytes below 2^8) and the
+// tile threshold 4 log2 y - 2 log2 P stays below 127 (bias B0 >= 0); blocks of
+// at most 2^30 y keep its offsets within 31 bits.
+static bool byte_path_ok(const PrimeTable *t, uint64_t y2, uint64_t P, uint64_t len)
+{
+    if (!t->pq || P < 1024 || y2 >= (1ull << 42) || len > (1ull << 30))
+        return false;
+    const double thr = kByteScale * std::log2((double)y2) - 2.0 * std::log2((double)P);
+    return thr < 126.0;
+}
+
 int sieve_block_enqueue(const PrimeTable *t, const SieveLaunch &L, cudaStream_t s)
 {
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(mu_sieve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kSieveWords * 4);
+        cudaFuncSetAttribute(mu_sieve_byte_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kByteTile + kByteSqWords * 4);
         attr_set = true;
     }
     const uint64_t y2 = L.y1 + L.len - 1;
@@ -445,13 +779,37 @@ int sieve_block_enqueue(const PrimeTable *t, const SieveLaunch &L, cudaStream_t 
         P = 7;
     const uint32_t np = prime_count_upto(t, P);
     const uint32_t np_small = prime_count_upto(t, 2047);
+    const bool bytes = byte_path_ok(t, y2, P, L.len) && getenv("MERTENS_SIEVE16") == nullptr;
     int launches = 0;
-    const uint32_t tiles = (uint32_t)((L.len + kSieveTile - 1) / kSieveTile);
     if (np > 4) {
-        sieve_block_prep_kernel<<<(np + 255) / 256, 256, 0, s>>>(L.y1, np, t->p, t->blk_r,
-                                                                 t->blk_qm);
+        sieve_block_prep_kernel<<<(np + 255) / 256, 256, 0, s>>>(
+            L.y1, np, t->p, t->blk_r, t->blk_qm, bytes ? t->blk_r2 : nullptr);
         ++launches;
     }
+    if (bytes) {
+        ByteArgs b;
+        b.y1 = L.y1;
+        b.len = (uint32_t)L.len;
+        b.np = np;
+        b.np_small = np_small < np ? np_small : np;
+        const uint32_t np_p = prime_count_upto(t, 127);
+        b.np_piece = np_p < b.np_small ? np_p : b.np_small;
+        b.thr_half = (float)(2.0 * std::log2((double)P));
+        b.pq = t->pq;
+        b.r = t->blk_r;
+        b.r2 = t->blk_r2;
+        b.pat8 = t->pat8;
+        b.patsq = t->patsq;
+        b.Mloc = L.Mloc;
+        b.segsum = L.segsum;
+        b.mu_out = L.mu_out;
+        b.mu_base = L.mu_base;
+        b.mu_end = L.mu_end;
+        const uint32_t btiles = (uint32_t)((L.len + kByteTile - 1) / kByteTile);
+        mu_sieve_byte_kernel<<<btiles, kSieveThreads, kByteTile + kByteSqWords * 4, s>>>(b);
+        ++launches;
+    }
+    const uint32_t tiles = bytes ? 0u : (uint32_t)((L.len + kSieveTile - 1) / kSieveTile);
     SieveArgs a;
     a.y1 = L.y1;
     a.len = L.len;
@@ -473,8 +831,10 @@ int sieve_block_enqueue(const PrimeTable *t, const SieveLaunch &L, cudaStream_t 
     a.mu_out = L.mu_out;
     a.mu_base = L.mu_base;
     a.mu_end = L.mu_end;
-    mu_sieve_kernel<<<tiles, kSieveThreads, kSieveWords * 4, s>>>(a);
-    ++launches;
+    if (tiles) {
+        mu_sieve_kernel<<<tiles, kSieveThreads, kSieveWords * 4, s>>>(a);
+        ++launches;
+    }
     if (L.mid)
         cudaEventRecord(L.mid, s);
     if (L.mid2)

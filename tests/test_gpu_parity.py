@@ -19,6 +19,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TILE = 32768
+BYTE_TILE = 131072
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -49,6 +50,12 @@ def gpu_array(n, u=0, block_len=0):
     (2**40 - 1000, TILE + 31),
     (999_983 * 999_983 - 300, 700),     # a prime square inside the window
     (1, 1), (2, 5), (7, 60),            # tiny windows
+    # byte sieve: tiles below and above the 2^26 switch to one threshold per
+    # tile, a ragged last tile, the top of its range (y < 2^42), and past it
+    (2**26 - 3 * BYTE_TILE + 5, 6 * BYTE_TILE + 3),
+    (2**41 + 12345, 2 * BYTE_TILE + 7),
+    (2**42 - BYTE_TILE - 77, BYTE_TILE + 70),
+    (2**42 + 5, 1000),
 ])
 def test_sieve_mu_matches_oracle(y1, length):
     mu = torch.empty(length + 16, dtype=torch.int8, device="cuda")
@@ -75,6 +82,22 @@ def test_sieve_M_with_carry_far_from_one():
     pm.mertens_sieve_M(y1, length, carry, M)
     ref = carry + np.cumsum(oracle.mu_window(y1, length).astype(np.int64))
     assert np.array_equal(M.cpu().numpy().astype(np.int64), ref)
+
+
+@pytest.mark.parametrize("y1,length", [(1, 3 * 10**6 + 11), (7 * 10**9 + 1, 4 * BYTE_TILE + 999)])
+def test_byte_and_halfword_sieves_agree(y1, length, monkeypatch):
+    """The byte kernel and the 16-bit kernel give the same M(y), and both
+    match the oracle's mu."""
+    carry = 0 if y1 == 1 else oracle.mertens(y1 - 1, L=10**6)
+    M8 = torch.empty(length, dtype=torch.int32, device="cuda")
+    pm.mertens_sieve_M(y1, length, carry, M8)
+    monkeypatch.setenv("MERTENS_SIEVE16", "1")
+    M16 = torch.empty(length, dtype=torch.int32, device="cuda")
+    pm.mertens_sieve_M(y1, length, carry, M16)
+    a, b = M8.cpu().numpy(), M16.cpu().numpy()
+    assert np.array_equal(a, b)
+    ref = carry + np.cumsum(oracle.mu_window(y1, length).astype(np.int64))
+    assert np.array_equal(a.astype(np.int64), ref)
 
 
 def test_sieve_rejects_bad_arguments():
