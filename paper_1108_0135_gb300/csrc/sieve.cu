@@ -315,52 +315,85 @@ struct ByteArgs {
     uint64_t mu_base, mu_end;
 };
 
-// Multiples of a prime p < 2048 in the tile offsets [lo, hi), lanes over them.
-// The step 32p is a multiple of 4, so each lane stays on one byte of the word
+// Small-prime job (p < 2048): the multiples of p in the tile offsets [lo, hi),
+// lanes over them.  Its descriptor, made in the kernel's prologue, is
+// {first multiple >= lo, hi, p | w(p) << 16, first multiple of p^2 >= lo or
+// kNone when p^2 > tile (that single square is marked in the prologue)}.
+// The step 32p is a multiple of 4, so each lane stays on one byte of its words
 // and its shifted weight is loop-invariant.
-__device__ __forceinline__ void byte_prime_warp(const ByteArgs &a, uint32_t *w, uint32_t *sq,
-                                                uint32_t t, uint32_t a0, uint32_t lo, uint32_t hi,
-                                                uint32_t lane)
+constexpr uint32_t kNone = 0xffffffffu;
+constexpr uint32_t kByteJobsMax = 512;  // 8 * 27 pieces (p < 128) + 278 primes below 2048
+
+__device__ __forceinline__ void byte_small_job(uint4 d, uint32_t *w, uint32_t *sq, uint32_t lane)
 {
+    const uint32_t p = d.z & 0xffffu;
+    const uint32_t yo = d.x + lane * p;
+    const uint32_t wsh = (d.z >> 16) << ((yo & 3u) << 3);
+    const uint32_t step = 8u * p;  // words per 32 multiples
+    const uint32_t end = (d.y + 3u - (yo & 3u)) >> 2;  // yo' < hi  <=>  yo' >> 2 < end
+#pragma unroll 4
+    for (uint32_t wi = yo >> 2; wi < end; wi += step)
+        atomicAdd(&w[wi], wsh);
+    if (d.w != kNone) {
+        const uint32_t p2 = p * p;  // <= tile
+        for (uint32_t y2o = d.w + lane * p2; y2o < d.y; y2o += 32u * p2)
+            atomicOr(&sq[y2o >> 5], 1u << (y2o & 31u));
+    }
+}
+
+// Descriptor of small-prime job i (see above); *single is the one multiple of
+// p^2 in the range when p^2 > tile, else kNone.
+__device__ __forceinline__ uint4 byte_small_desc(const ByteArgs &a, uint32_t i, uint32_t jp,
+                                                 uint32_t a0, uint32_t tl, uint32_t *single)
+{
+    uint32_t t, lo, hi;
+    if (i < jp) {
+        t = 4 + (i >> 3);
+        lo = (i & 7u) * (kByteTile / 8);
+        hi = min(tl, lo + kByteTile / 8);
+    } else {
+        t = a.np_piece + (i - jp);
+        lo = 0;
+        hi = tl;
+    }
+    *single = kNone;
+    if (lo >= hi)
+        return make_uint4(hi, hi, 11u, kNone);
     const uint4 q = a.pq[t];
     const uint32_t p = q.x;
     const uint32_t v = a.r[t] + a0 + lo;  // < 2^31
     const uint32_t rem = v - div_magic32(v, q.y, q.w & 255u) * p;
-    const uint32_t yo = lo + (rem ? p - rem : 0u) + lane * p;
-    const uint32_t wsh = (q.w >> 16) << ((yo & 3u) << 3);
-    const uint32_t step = 8u * p;  // words per 32 multiples
-    const uint32_t end = (hi + 3u - (yo & 3u)) >> 2;  // yo' < hi  <=>  yo' >> 2 < end
-#pragma unroll 4
-    for (uint32_t wi = yo >> 2; wi < end; wi += step)
-        atomicAdd(&w[wi], wsh);
     const uint32_t p2 = p * p;
     const uint32_t v2 = (uint32_t)a.r2[t] + a0 + lo;  // < 2^31
     const uint32_t rem2 = v2 - div_magic32(v2, q.z, (q.w >> 8) & 255u) * p2;
-    for (uint32_t y2o = lo + (rem2 ? p2 - rem2 : 0u) + lane * p2; y2o < hi; y2o += 32u * p2)
-        atomicOr(&sq[y2o >> 5], 1u << (y2o & 31u));
+    uint32_t s2 = lo + (rem2 ? p2 - rem2 : 0u);
+    if (p2 > (uint32_t)kByteTile) {
+        *single = s2 < hi ? s2 : kNone;
+        s2 = kNone;
+    }
+    return make_uint4(lo + (rem ? p - rem : 0u), hi, p | ((q.w >> 16) << 16), s2);
 }
 
-// One prime p >= 2048 per lane over the whole tile; p^2 > tile, so at most
-// one multiple of p^2.
-__device__ __forceinline__ void byte_prime_lane(const ByteArgs &a, uint32_t *w, uint32_t *sq,
-                                                uint32_t t, uint32_t a0, uint32_t tl)
+// Hits of one prime p >= 2048 (one lane) over the whole tile; p^2 > tile, so
+// at most one multiple of p^2.
+__device__ __forceinline__ void byte_large_prime(uint4 q, uint32_t r, uint64_t r2, uint32_t *w,
+                                                 uint32_t *sq, uint32_t a0, uint32_t tl)
 {
-    const uint4 q = a.pq[t];
     const uint32_t p = q.x;
     const uint32_t wt = q.w >> 16;
-    const uint32_t v = a.r[t] + a0;  // < 2^31
+    const uint32_t v = r + a0;  // < 2^31
     const uint32_t rem = v - div_magic32(v, q.y, q.w & 255u) * p;
     for (uint32_t yo = rem ? p - rem : 0u; yo < tl; yo += p)
         atomicAdd(&w[yo >> 2], __funnelshift_l(0u, wt, yo << 3));
     uint64_t o2;
     if (q.z) {  // p^2 < 2^30: 32-bit division
         const uint32_t p2 = p * p;
-        const uint32_t v2 = (uint32_t)a.r2[t] + a0;  // < 2^31
+        const uint32_t v2 = (uint32_t)r2 + a0;  // < 2^31
         const uint32_t rem2 = v2 - div_magic32(v2, q.z, (q.w >> 8) & 255u) * p2;
         o2 = rem2 ? p2 - rem2 : 0u;
     } else {  // p^2 >= 2^30 > a0: y1 mod p^2 + a0 < 2 p^2
         const uint64_t p2 = (uint64_t)p * p;
-        uint64_t v2 = a.r2[t] + a0;
+        uint64_t v2 = r2 + a0;
         if (v2 >= p2)
             v2 -= p2;
         o2 = v2 ? p2 - v2 : 0u;
@@ -381,13 +414,21 @@ __global__ void __launch_bounds__(kSieveThreads, 1) mu_sieve_byte_kernel(ByteArg
     uint32_t *w = reinterpret_cast<uint32_t *>(sb);  // kByteWords words, four y each
     uint32_t *sq = w + kByteWords;                     // kByteSqWords words, 32 y each
     __shared__ uint32_t s_job;
+    __shared__ uint4 s_jd[kByteJobsMax];
     const uint32_t a0 = blockIdx.x * (uint32_t)kByteTile;
     const uint64_t t1 = a.y1 + a0;
     const uint32_t tl = min(a.len - a0, (uint32_t)kByteTile);
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t jp = a.np_piece > 4 ? 8u * (a.np_piece - 4) : 0u;
+    const uint32_t js = jp + (a.np_small - a.np_piece);  // small-prime jobs (<= kByteJobsMax)
+    const uint32_t jobs = js + (a.np - a.np_small + 63u) / 64u;
 
-    // pre-sieve pattern: bytes of 2, 3, 5, 7 and square flags of 4, 9, 25, 49
+    // prologue: small-prime job descriptors (a thread each), and the
+    // pre-sieve pattern (bytes of 2, 3, 5, 7, square flags of 4, 9, 25, 49)
+    uint32_t single = kNone;
     {
+        if (threadIdx.x < js)
+            s_jd[threadIdx.x] = byte_small_desc(a, threadIdx.x, jp, a0, tl, &single);
         const uint32_t ph = (uint32_t)(t1 % kPatternPeriod);
         const uint4 *src = a.pat8 + (size_t)(ph & 15u) * (kPat8Len / 16) + (ph >> 4);
 #pragma unroll 4
@@ -400,10 +441,12 @@ __global__ void __launch_bounds__(kSieveThreads, 1) mu_sieve_byte_kernel(ByteArg
             s_job = 0;
     }
     __syncthreads();
+    if (single != kNone)
+        atomicOr(&sq[single >> 5], 1u << (single & 31u));
 
-    const uint32_t jp = a.np_piece > 4 ? 8u * (a.np_piece - 4) : 0u;
-    const uint32_t js = jp + (a.np_small - a.np_piece);
-    const uint32_t jobs = js + (a.np - a.np_small + 31u) / 32u;
+    // jobs, largest first, handed out through a shared counter: small-prime
+    // jobs (a warp over the multiples of one prime), then 64 primes >= 2048 at
+    // a time (two per lane, the second one's loads in flight during the first)
     for (;;) {
         uint32_t job = 0;
         if (lane == 0)
@@ -411,17 +454,27 @@ __global__ void __launch_bounds__(kSieveThreads, 1) mu_sieve_byte_kernel(ByteArg
         job = __shfl_sync(0xffffffffu, job, 0);
         if (job >= jobs)
             break;
-        if (job < jp) {
-            const uint32_t k = job & 7u;
-            const uint32_t lo = k * (kByteTile / 8), hi = min(tl, (k + 1) * (kByteTile / 8));
-            if (lo < hi)
-                byte_prime_warp(a, w, sq, 4 + (job >> 3), a0, lo, hi, lane);
-        } else if (job < js) {
-            byte_prime_warp(a, w, sq, a.np_piece + (job - jp), a0, 0, tl, lane);
+        if (job < js) {
+            byte_small_job(s_jd[job], w, sq, lane);
         } else {
-            const uint32_t t = a.np_small + (job - js) * 32u + lane;
-            if (t < a.np)
-                byte_prime_lane(a, w, sq, t, a0, tl);
+            const uint32_t t0 = a.np_small + (job - js) * 64u + lane, t1p = t0 + 32u;
+            uint4 q0 = make_uint4(0, 0, 0, 0), q1 = q0;
+            uint32_t r0 = 0, r1 = 0;
+            uint64_t r20 = 0, r21 = 0;
+            if (t0 < a.np) {
+                q0 = a.pq[t0];
+                r0 = a.r[t0];
+                r20 = a.r2[t0];
+            }
+            if (t1p < a.np) {
+                q1 = a.pq[t1p];
+                r1 = a.r[t1p];
+                r21 = a.r2[t1p];
+            }
+            if (t0 < a.np)
+                byte_large_prime(q0, r0, r20, w, sq, a0, tl);
+            if (t1p < a.np)
+                byte_large_prime(q1, r1, r21, w, sq, a0, tl);
         }
     }
     __syncthreads();
