@@ -72,14 +72,18 @@ int mertens_set_allocator(mertens_alloc_fn alloc, mertens_free_fn release, void 
  *
  *   out        receives the plan (owned by the caller; free with
  *              mertens_destroy).
- *   n          `count` targets, each 1 <= n_i < 2^63 in this build
- *              (MERTENS_ENOTSUP at or above 2^63).  Copied; the caller keeps
- *              ownership.
+ *   n          `count` targets, each 1 <= n_i < 2^127 (else MERTENS_EINVAL).
+ *              Array entries with k = floor(n_i/x) >= 2^63 (x <= n_i/2^63,
+ *              so only for n_i >= 2^63) are computed with two-word (128-bit)
+ *              quotients (the paper, Sec. 5, uses 128-bit integers there);
+ *              all others with one-word quotients.  Copied; the caller
+ *              keeps ownership.
  *   u          sieve limit shared by all targets.  {0,0} = chosen per target
  *              by the library (see mertens_tuning).  Otherwise it must
  *              satisfy floor(sqrt(n_i)) < u <= n_i for every i (u = 1 is
- *              allowed for n_i = 1), else MERTENS_EINVAL.  Each target's array
- *              has X_i = floor(n_i/u_i) entries (Sec. 2).
+ *              allowed for n_i = 1), else MERTENS_EINVAL.  u < 2^64 (else
+ *              MERTENS_ENOTSUP).  Each target's array has X_i = floor(n_i/u_i)
+ *              entries (Sec. 2); X_i >= 2^32 is MERTENS_ENOTSUP.
  *   block_len  length of a sieve block in y (Sec. 3, "divide calculations
  *              into blocks of y"); 0 = chosen by the library.  Any value >= 1
  *              is honoured exactly.

@@ -112,6 +112,40 @@ static uint64_t isqrt64(uint64_t v)
     return r;
 }
 
+typedef unsigned __int128 u128;
+constexpr u128 kTwo63 = (u128)1 << 63;
+
+static u128 to_u128(mertens_u128 v) { return ((u128)v.hi << 64) | v.lo; }
+
+// floor(sqrt(v)) for v < 2^128: a double estimate, one Newton step, then
+// exact +-1 corrections on 128-bit squares.
+static uint64_t isqrt128(u128 v)
+{
+    if (v < kTwo63)
+        return isqrt64((uint64_t)v);
+    u128 r = (u128)std::sqrt((double)v);
+    r = (r + v / r) / 2;
+    while (r * r > v)
+        --r;
+    while ((r + 1) * (r + 1) <= v)
+        ++r;
+    return (uint64_t)r;
+}
+
+// Entries with k at or above this take the two-word kernel: 2^63, or a
+// lower MERTENS_WIDE_FROM (so that tests can run that kernel on targets the
+// oracle reaches).  k = 1 never does (the split form needs k >= 2).
+static u128 wide_threshold()
+{
+    const char *e = getenv("MERTENS_WIDE_FROM");
+    if (e) {
+        const unsigned long long v = strtoull(e, nullptr, 10);
+        if (v >= 2 && v < (1ull << 63))
+            return v;
+    }
+    return kTwo63;
+}
+
 }  // namespace mert
 
 using namespace mert;
@@ -133,7 +167,7 @@ struct mertens_plan_s {
     std::vector<std::pair<void *, size_t>> allocs;
     // targets
     size_t nq = 0;
-    std::vector<uint64_t> n, u, X, off;
+    std::vector<uint64_t> n, n_hi, u, X, off;
     std::vector<uint64_t> direct, gathered, ymax_q;
     uint64_t nent = 0;
     uint64_t y_max = 0, block_len = 0, nblocks = 0, ydense = 0, jmax = 0, mg_n = 0;
@@ -172,6 +206,11 @@ struct mertens_plan_s {
     DenseItem *ditems = nullptr;
     uint32_t nitems = 0;
     QueryDev *dqs = nullptr;
+    // entries with k >= 2^63 (targets n >= 2^63) and the wide kernel's
+    // grid width per block (0: no terms in the block)
+    std::vector<WideEntry> wide;
+    WideEntry *dwide = nullptr;
+    std::vector<uint32_t> wide_grid;
     bool mg_built = false;
     // run state
     cudaEvent_t done = nullptr;
@@ -216,14 +255,15 @@ static double dense_factor(const mertens_tuning &t)
 }
 
 // Shape of one target (host only): X, y_max and the closed-form term counts.
-static int describe_target(uint64_t n, uint64_t u, uint64_t *X, uint64_t *direct,
+static int describe_target(u128 n, uint64_t u, uint64_t *X, uint64_t *direct,
                            uint64_t *gathered)
 {
-    *X = n / u;
+    *X = (uint64_t)(n / u);
     uint64_t d = 0, g = 0;
     for (uint64_t x = 1; x <= *X; ++x) {
-        const uint64_t k = n / x, s = isqrt64(k);
-        const uint64_t jlo = k / u + 1, jhi = k / (s + 1);
+        const u128 k = n / x;
+        const uint64_t s = isqrt128(k);
+        const uint64_t jlo = *X / x + 1, jhi = (uint64_t)(k / ((u128)s + 1));
         d += s;
         if (jhi >= jlo)
             g += jhi - jlo + 1;
@@ -237,19 +277,20 @@ static int describe_target(uint64_t n, uint64_t u, uint64_t *X, uint64_t *direct
 // ~count sqrt(n n/u), balanced at u ~ (count n)^(2/3) (Sec. 2); the extra
 // count^(-1/5) and f = 0.45 are what the autotuner measured on GB300 for
 // single targets (0.45) and batches of 8 (0.3).
-static uint64_t auto_u(uint64_t n, size_t count, const mertens_tuning &t)
+static uint64_t auto_u(u128 n, size_t count, const mertens_tuning &t)
 {
     if (n <= 3)
-        return n;
+        return (uint64_t)n;
     const char *e = getenv("MERTENS_U_FACTOR");
     const double f = e ? atof(e) : (t.u_factor > 0 ? t.u_factor : 0.45);
-    uint64_t u = (uint64_t)(f * std::pow((double)n * (double)count, 2.0 / 3.0) *
-                            std::pow((double)count, -0.2));
-    const uint64_t r = isqrt64(n);
+    const double ud = f * std::pow((double)n * (double)count, 2.0 / 3.0) *
+                      std::pow((double)count, -0.2);
+    uint64_t u = ud >= 1.8e19 ? UINT64_MAX : (uint64_t)ud;
+    const uint64_t r = isqrt128(n);
     if (u <= r)
         u = r + 1;
-    if (u > n)
-        u = n;
+    if ((u128)u > n)
+        u = (uint64_t)n;
     return u;
 }
 
@@ -269,13 +310,28 @@ size_t plan_device_bytes(mertens_plan_t p)
 }
 }  // namespace mert
 
-static int check_u(uint64_t n, uint64_t u)
+static int check_u(u128 n, uint64_t u)
 {
     if (n == 1)
         return u == 1 ? MERTENS_OK : MERTENS_EINVAL;
-    const uint64_t r = isqrt64(n);
-    if (u <= r || u > n)
+    const uint64_t r = isqrt128(n);
+    if (u <= r || (u128)u > n)
         return MERTENS_EINVAL;
+    return MERTENS_OK;
+}
+
+// Limits of this build: n < 2^127 (u < 2^64 then follows from u <= n for
+// n < 2^64, and is required above it), X = floor(n/u) < 2^32 entries.
+static int check_n(mertens_u128 n, const char *who, size_t i)
+{
+    if (n.lo == 0 && n.hi == 0) {
+        set_last_error("%s: n[%zu] = 0", who, i);
+        return MERTENS_EINVAL;
+    }
+    if (n.hi >= (1ull << 63)) {
+        set_last_error("%s: n[%zu] >= 2^127", who, i);
+        return MERTENS_EINVAL;
+    }
     return MERTENS_OK;
 }
 
@@ -313,31 +369,38 @@ int mertens_set_allocator(mertens_alloc_fn alloc, mertens_free_fn release, void 
 
 int mertens_describe(mertens_u128 n, mertens_u128 u, mertens_query_info *info)
 {
-    if (!info || (n.lo == 0 && n.hi == 0)) {
-        set_last_error("mertens_describe: n must be >= 1");
+    if (!info) {
+        set_last_error("mertens_describe: NULL info");
         return MERTENS_EINVAL;
     }
-    if (n.hi != 0 || n.lo >= (1ull << 63) || u.hi != 0) {
-        set_last_error("mertens_describe: n >= 2^63 is not supported by this build");
+    if (check_n(n, "mertens_describe", 0) != MERTENS_OK)
+        return MERTENS_EINVAL;
+    if (u.hi != 0) {
+        set_last_error("mertens_describe: u >= 2^64 is not supported by this build");
         return MERTENS_ENOTSUP;
     }
-    uint64_t uu = u.lo ? u.lo : auto_u(n.lo, 1, tuning_now());
-    if (check_u(n.lo, uu) != MERTENS_OK) {
+    const u128 nn = to_u128(n);
+    uint64_t uu = u.lo ? u.lo : auto_u(nn, 1, tuning_now());
+    if (check_u(nn, uu) != MERTENS_OK) {
         set_last_error("mertens_describe: u must satisfy floor(sqrt(n)) < u <= n");
         return MERTENS_EINVAL;
+    }
+    if (nn / uu >= ((u128)1 << 32)) {
+        set_last_error("mertens_describe: n/u >= 2^32 array entries");
+        return MERTENS_ENOTSUP;
     }
     memset(info, 0, sizeof(*info));
     info->n = n;
     info->u.lo = uu;
     uint64_t X, d, g;
-    describe_target(n.lo, uu, &X, &d, &g);
+    describe_target(nn, uu, &X, &d, &g);
     info->X = X;
     info->direct_terms = d;
     info->gathered_terms = g;
     // largest y read: the direct range ends at s <= sqrt(n); the gathered
     // range of x = 1 ends at floor(n/(X+1)).
-    const uint64_t r = isqrt64(n.lo);
-    const uint64_t yg = n.lo / (X + 1);
+    const uint64_t r = isqrt128(nn);
+    const uint64_t yg = (uint64_t)(nn / ((u128)X + 1));
     info->y_max = std::max(r, yg);
     return MERTENS_OK;
 }
@@ -357,19 +420,19 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
         return MERTENS_ENOTSUP;
     }
     for (size_t i = 0; i < count; ++i) {
-        if (n[i].lo == 0 && n[i].hi == 0) {
-            set_last_error("mertens_plan: n[%zu] = 0", i);
+        if (check_n(n[i], "mertens_plan", i) != MERTENS_OK)
             return MERTENS_EINVAL;
-        }
-        if (n[i].hi != 0 || n[i].lo >= (1ull << 63)) {
-            set_last_error("mertens_plan: n[%zu] >= 2^63 needs the two-word path (not built)", i);
-            return MERTENS_ENOTSUP;
-        }
-        if (u.lo != 0 && check_u(n[i].lo, u.lo) != MERTENS_OK) {
-            set_last_error("mertens_plan: u = %llu invalid for n[%zu] = %llu "
+        const u128 nn = to_u128(n[i]);
+        if (u.lo != 0 && check_u(nn, u.lo) != MERTENS_OK) {
+            set_last_error("mertens_plan: u = %llu invalid for n[%zu] "
                            "(need floor(sqrt(n)) < u <= n)",
-                           (unsigned long long)u.lo, i, (unsigned long long)n[i].lo);
+                           (unsigned long long)u.lo, i);
             return MERTENS_EINVAL;
+        }
+        const uint64_t uu = u.lo ? u.lo : auto_u(nn, count, tn);
+        if (nn / uu >= ((u128)1 << 32)) {
+            set_last_error("mertens_plan: n[%zu]/u >= 2^32 array entries", i);
+            return MERTENS_ENOTSUP;
         }
     }
     mertens_plan_s *p = new (std::nothrow) mertens_plan_s();
@@ -384,26 +447,61 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
     std::vector<uint64_t> K, JLO, JC0, YCE;
     std::vector<Group> groups;
     for (size_t i = 0; i < count; ++i) {
-        const uint64_t nn = n[i].lo;
+        const u128 nn = to_u128(n[i]);
         const uint64_t uu = u.lo ? u.lo : auto_u(nn, count, tn);
-        const uint64_t X = nn / uu;
-        p->n.push_back(nn);
+        const uint64_t X = (uint64_t)(nn / uu);
+        p->n.push_back((uint64_t)nn);
+        p->n_hi.push_back((uint64_t)(nn >> 64));
         p->u.push_back(uu);
         p->X.push_back(X);
         p->off.push_back(K.size());
         uint64_t d = 0, g = 0, ymq = 0;
         std::vector<uint64_t> S_(32), VH(32);
+        std::vector<uint8_t> WD(32);
+        const u128 wide_from = wide_threshold();
         for (uint64_t x0 = 1; x0 <= X; x0 += 32) {
             const uint32_t cnt = (uint32_t)std::min<uint64_t>(32, X - x0 + 1);
-            uint64_t lo = 0, hi = UINT64_MAX;
+            uint64_t lo = 0, hi = UINT64_MAX, kf = 0;
+            bool any_wide = false;
             for (uint32_t t = 0; t < cnt; ++t) {
-                const uint64_t x = x0 + t, k = nn / x, s = isqrt64(k);
-                const uint64_t jlo = k / uu + 1, jhi = k / (s + 1);
+                const uint64_t x = x0 + t;
+                const u128 k128 = nn / x;
+                const uint64_t jlo = X / x + 1;  // = floor(k/u) + 1
+                if (k128 >= wide_from) {
+                    // two-word entry: its own kernel; k = 0 (no terms) here
+                    WideEntry W;
+                    W.k_lo = (uint64_t)k128;
+                    W.k_hi = (uint64_t)(k128 >> 64);
+                    W.s = isqrt128(k128);
+                    W.jlo = jlo;
+                    W.jhi = (uint64_t)(k128 / ((u128)W.s + 1));
+                    W.e = K.size();
+                    p->wide.push_back(W);
+                    d += W.s;
+                    uint64_t need = W.s;
+                    if (W.jhi >= W.jlo) {
+                        g += W.jhi - W.jlo + 1;
+                        need = std::max(need, (uint64_t)(k128 / W.jlo));
+                    }
+                    ymq = std::max(ymq, need);
+                    S_[t] = 0;
+                    VH[t] = 0;
+                    WD[t] = 1;
+                    any_wide = true;
+                    K.push_back(0);
+                    JLO.push_back(1);
+                    continue;
+                }
+                const uint64_t k = (uint64_t)k128, s = isqrt64(k);
+                const uint64_t jhi = k / (s + 1);
                 // valid dense cut-offs: [s, floor(k/jlo) - 1] when the entry
                 // has gathered terms, else exactly s
                 const uint64_t vh = (jlo <= jhi) ? (k / jlo - 1) : s;
                 S_[t] = s;
                 VH[t] = vh;
+                WD[t] = 0;
+                if (kf == 0)
+                    kf = k;
                 lo = std::max(lo, s);
                 hi = std::min(hi, vh);
                 d += s;
@@ -412,14 +510,23 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
                 K.push_back(k);
                 JLO.push_back(jlo);
             }
-            const uint64_t kf = nn / x0;
             uint64_t target = (uint64_t)(dc * std::sqrt((double)kf));
             target = ((target + 1 + kChunk - 1) / kChunk) * kChunk - 1;  // chunk aligned
             Group G;
             G.first = (uint32_t)(K.size() - cnt);
             G.count = cnt;
             G.pad = 0;
-            if (lo <= hi) {
+            if (any_wide) {
+                // per-entry cut-offs; the two-word entries take none
+                G.pred = 1;
+                G.yc = 0;
+                for (uint32_t t = 0; t < cnt; ++t) {
+                    const uint64_t yc =
+                        WD[t] ? 0 : std::min(std::max(target, S_[t]), VH[t]);
+                    YCE.push_back(yc);
+                    G.yc = std::max(G.yc, yc);
+                }
+            } else if (lo <= hi) {
                 const uint64_t yc = std::min(std::max(target, lo), hi);
                 G.pred = 0;
                 G.yc = yc;
@@ -437,6 +544,10 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
             groups.push_back(G);
             for (uint32_t t = 0; t < cnt; ++t) {
                 const size_t e = G.first + t;
+                if (WD[t]) {
+                    JC0.push_back(0);
+                    continue;
+                }
                 const uint64_t k = K[e], yc = YCE[e];
                 const uint64_t jc0 = k / (yc + 1);
                 JC0.push_back(jc0);
@@ -521,8 +632,10 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
     for (size_t i = 0; i < count; ++i) {
         uint64_t run = UINT64_MAX;
         for (uint64_t x = 0; x < p->X[i]; ++x) {
-            run = std::min(run, YCE[p->off[i] + x]);
-            ycmin[p->off[i] + x] = run;
+            const size_t e = p->off[i] + x;
+            if (K[e] != 0)  // two-word entries have no terms here
+                run = std::min(run, YCE[e]);
+            ycmin[e] = run;
         }
     }
     const double kItemWork = 2.0e5;
@@ -534,7 +647,8 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
         // a quarter of the entries it must check (all of them, E).
         double acc = 0;
         for (size_t i = 0; i < count; ++i)
-            acc += (double)p->n[i] * std::log((double)std::max<uint64_t>(p->X[i], 2));
+            acc += ((double)p->n[i] + 18446744073709551616.0 * (double)p->n_hi[i]) *
+                   std::log((double)std::max<uint64_t>(p->X[i], 2));
         const double E = (double)std::max<uint64_t>(p->nent, 1);
         const double gs = tn.gather_scale > 0 ? tn.gather_scale : 1.0;
         uint64_t ys = (uint64_t)(gs * std::min(std::sqrt(acc / 2.0),
@@ -612,6 +726,21 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
         }
     }
     p->gblk.push_back((uint32_t)gitems.size());
+    // ---- two-word entries: grid width per block ----
+    if (!p->wide.empty()) {
+        p->wide_grid.assign(p->nblocks, 0);
+        for (uint64_t b = 0; b < p->nblocks; ++b) {
+            const uint64_t y1 = 1 + b * block_len;
+            const uint64_t y2 = std::min(y1 + block_len - 1, p->y_max);
+            uint64_t most = 0;
+            for (const WideEntry &W : p->wide) {
+                uint64_t nd, ja, ng;
+                wide_ranges(W, y1, y2, &nd, &ja, &ng);
+                most = std::max(most, nd + ng);
+            }
+            p->wide_grid[b] = (uint32_t)((most + kWideUnitsPerCta - 1) / kWideUnitsPerCta);
+        }
+    }
 
     // ---- device buffers ----
     int rc = MERTENS_OK;
@@ -662,6 +791,8 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
     p->dgroups = p->alloc<Group>(sg.size());
     p->ditems = p->alloc<DenseItem>(items.size());
     p->dqs = p->alloc<QueryDev>(count);
+    if (!p->wide.empty())
+        p->dwide = p->alloc<WideEntry>(p->wide.size());
     for (auto &a : p->allocs)
         if (!a.first)
             rc = MERTENS_ENOMEM;
@@ -672,7 +803,7 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
                     !p->dcounter_dense || !p->dcounter_gather ||
                     !p->dgitems || !p->dcarry || !p->derr || !p->dcounter || !p->dMG ||
                     !p->ddl_m || !p->ddl_yo || !p->ddl_cnt || !p->dgroups || !p->ditems ||
-                    !p->dqs;
+                    !p->dqs || (!p->wide.empty() && !p->dwide);
     if (any_null)
         rc = MERTENS_ENOMEM;
     if (rc == MERTENS_OK) {
@@ -710,6 +841,9 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
             cudaMemcpy(p->ditems, items.data(), items.size() * sizeof(DenseItem),
                        cudaMemcpyHostToDevice);
         cudaMemcpy(p->dqs, qs.data(), count * sizeof(QueryDev), cudaMemcpyHostToDevice);
+        if (!p->wide.empty())
+            cudaMemcpy(p->dwide, p->wide.data(), p->wide.size() * sizeof(WideEntry),
+                       cudaMemcpyHostToDevice);
         if (!gtiles.empty())
             cudaMemcpy(p->dgtiles, gtiles.data(), gtiles.size() * sizeof(GatherTile),
                        cudaMemcpyHostToDevice);
@@ -718,7 +852,7 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
                        cudaMemcpyHostToDevice);
         p->h2d_bytes = 4 * E * 8 + sg.size() * sizeof(Group) + items.size() * sizeof(DenseItem) +
                        count * sizeof(QueryDev) + gtiles.size() * sizeof(GatherTile) +
-                       gitems.size() * sizeof(GatherItem);
+                       gitems.size() * sizeof(GatherItem) + p->wide.size() * sizeof(WideEntry);
         if (cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming) != cudaSuccess ||
             cudaGetLastError() != cudaSuccess)
             rc = MERTENS_ECUDA;
@@ -988,6 +1122,21 @@ static int run_enqueue(mertens_plan_s *p, cudaStream_t origin, uint64_t *out)
             if (r < 0)
                 goto fail;
             launches += r;
+            if (!p->wide.empty() && p->wide_grid[b]) {
+                WideArgs wa;
+                wa.W = p->dwide;
+                wa.y1 = y1;
+                wa.y2 = y2;
+                wa.Mloc = p->dMloc[buf];
+                wa.segoff = p->dsegoff[buf];
+                wa.S = p->dS;
+                ev_begin(p, kPhGather, s, &pe);
+                r = wide_update_enqueue(wa, (uint32_t)p->wide.size(), p->wide_grid[b], s);
+                ev_end(p, s, &pe);
+                if (r < 0)
+                    goto fail;
+                launches += r;
+            }
             if (!serial)
                 cudaEventRecord(p->ev_upd[b], su);
         }
@@ -1164,6 +1313,7 @@ int mertens_plan_info(mertens_plan_t p, size_t i, mertens_query_info *info)
         return MERTENS_EINVAL;
     memset(info, 0, sizeof(*info));
     info->n.lo = p->n[i];
+    info->n.hi = p->n_hi[i];
     info->u.lo = p->u[i];
     info->X = p->X[i];
     info->y_max = p->ymax_q[i];

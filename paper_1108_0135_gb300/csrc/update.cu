@@ -546,6 +546,66 @@ int sparse_block_enqueue(const SparseBlockArgs &b, const SparseArgs &a, uint32_t
     return cudaGetLastError() == cudaSuccess ? launches : -1;
 }
 
+// ---------------------------------------------------------------------------
+// Entries with k >= 2^63 (one CTA row per entry, grid.y = entries): the
+// block's direct terms y in [y1, min(y2, s)] and gathered terms j in
+// [max(jlo, floor(k/(y2+1))+1), min(jhi, floor(k/y1))], numbered as one unit
+// range; each thread takes kWidePer consecutive units.  Quotients are exact
+// 128-by-64 divisions; sums are mod 2^64 (the direct differences are taken
+// on the low words, which is the same mod 2^64).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kWideThreads) wide_update_kernel(WideArgs a)
+{
+    __shared__ uint64_t red[kWideThreads / 32];
+    const WideEntry W = a.W[blockIdx.y];
+    const unsigned __int128 k = ((unsigned __int128)W.k_hi << 64) | W.k_lo;
+    uint64_t nd, ja, ng;
+    wide_ranges(W, a.y1, a.y2, &nd, &ja, &ng);
+    const uint64_t units = nd + ng;
+    const uint64_t u0 = (uint64_t)blockIdx.x * kWideUnitsPerCta + (uint64_t)threadIdx.x * kWidePer;
+    const uint64_t u1 = u0 + kWidePer < units ? u0 + kWidePer : units;
+    uint64_t acc = 0;
+    uint64_t u = u0;
+    if (u < u1 && u < nd) {
+        // direct: y = y1 + u, consecutive; q = floor(k/y) carried along
+        uint64_t y = a.y1 + u;
+        uint64_t q = (uint64_t)(k / y);
+        const uint64_t ue = u1 < nd ? u1 : nd;
+        for (; u < ue; ++u, ++y) {
+            const uint64_t qn = (uint64_t)(k / ((unsigned __int128)y + 1));
+            const uint64_t i = y - a.y1;
+            const int64_t M = a.segoff[i >> kSegShift] + (int64_t)a.Mloc[i];
+            acc += (uint64_t)M * (q - qn);
+            q = qn;
+        }
+    }
+    for (; u < u1; ++u) {
+        // gathered: y = floor(k/j) in [y1, y2]
+        const uint64_t j = ja + (u - nd);
+        const uint64_t i = (uint64_t)(k / j) - a.y1;
+        acc += (uint64_t)(a.segoff[i >> kSegShift] + (int64_t)a.Mloc[i]);
+    }
+    acc = warp_sum_u64(acc);
+    if ((threadIdx.x & 31) == 0)
+        red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint64_t t = 0;
+        for (int w = 0; w < kWideThreads / 32; ++w)
+            t += red[w];
+        if (t)
+            atomicAdd(reinterpret_cast<unsigned long long *>(a.S + W.e), (unsigned long long)t);
+    }
+}
+
+int wide_update_enqueue(const WideArgs &a, uint32_t nw, uint32_t grid_x, cudaStream_t s)
+{
+    if (nw == 0 || grid_x == 0)
+        return 0;
+    wide_update_kernel<<<dim3(grid_x, nw), kWideThreads, 0, s>>>(a);
+    return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
 int gather_tiles_enqueue(const GatherArgs &a, cudaStream_t s)
 {
     static bool attr = false;

@@ -97,7 +97,49 @@ struct GatherArgs {
     uint32_t ctas_per_sm;  // 0: as many as fit; else at most this many per SM
 };
 
+// Array entry with k = floor(n/x) >= 2^63 (targets n >= 2^63 only): its k
+// needs two words, so it takes the paper's split form directly -- direct terms
+// M(y)(floor(k/y) - floor(k/(y+1))) for y <= s and gathered terms
+// M(floor(k/j)) for j in [jlo, jhi] -- with 128-bit quotients, in its own
+// kernel.  The 64-bit kernels see such an entry as k = 0 (no terms).
+struct WideEntry {
+    uint64_t k_lo, k_hi;  // k
+    uint64_t s;           // floor(sqrt(k))
+    uint64_t jlo, jhi;    // floor(X/x) + 1, floor(k/(s+1))
+    uint64_t e;           // global entry index
+};
+
+struct WideArgs {
+    const WideEntry *W;
+    uint64_t y1, y2;  // the block
+    const int16_t *Mloc;
+    const int64_t *segoff;
+    uint64_t *S;
+};
+
+// Units (terms) per CTA of the wide kernel, and the units of entry W in the
+// block [y1, y2] (host and device).
+constexpr int kWideThreads = 256;
+constexpr int kWidePer = 16;
+constexpr uint64_t kWideUnitsPerCta = (uint64_t)kWideThreads * kWidePer;
+
+__host__ __device__ inline void wide_ranges(const WideEntry &W, uint64_t y1, uint64_t y2,
+                                            uint64_t *nd, uint64_t *ja, uint64_t *ng)
+{
+    const unsigned __int128 k = ((unsigned __int128)W.k_hi << 64) | W.k_lo;
+    const uint64_t dl = y2 < W.s ? y2 : W.s;
+    *nd = y1 <= dl ? dl - y1 + 1 : 0;
+    // j with floor(k/j) in [y1, y2]: floor(k/(y2+1)) < j <= floor(k/y1)
+    const unsigned __int128 q2 = k / ((unsigned __int128)y2 + 1) + 1;
+    const unsigned __int128 q1 = k / y1;
+    const unsigned __int128 a = q2 > W.jlo ? q2 : (unsigned __int128)W.jlo;
+    const unsigned __int128 b = q1 < W.jhi ? q1 : (unsigned __int128)W.jhi;
+    *ja = (uint64_t)a;
+    *ng = b >= a ? (uint64_t)(b - a + 1) : 0;
+}
+
 int magic_table_enqueue(uint64_t *MG, uint64_t nd, cudaStream_t s);
+int wide_update_enqueue(const WideArgs &a, uint32_t nw, uint32_t grid_x, cudaStream_t s);
 int dense_list_enqueue(const int8_t *mu_aux, uint64_t ydense, const uint64_t *MG, uint64_t *dl_m,
                        uint16_t *dl_yo, uint32_t *dl_cnt, cudaStream_t s);
 int dense_update_enqueue(const DenseArgs &a, cudaStream_t s);

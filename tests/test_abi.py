@@ -59,7 +59,8 @@ def test_describe_full_size_counts():
     (0, 0, pm.MERTENS_EINVAL),
     (100, 10, pm.MERTENS_EINVAL),       # u must exceed floor(sqrt(n))
     (100, 101, pm.MERTENS_EINVAL),      # u must not exceed n
-    (2**63, 0, pm.MERTENS_ENOTSUP),     # two-word path not in this build
+    (2**127, 0, pm.MERTENS_EINVAL),     # n must be below 2^127
+    (2**80, 2**41, pm.MERTENS_ENOTSUP), # 2^39 array entries
 ])
 def test_invalid_arguments_rejected_without_gpu(n, u, code):
     with pytest.raises(pm.MertensError) as ei:
@@ -68,6 +69,28 @@ def test_invalid_arguments_rejected_without_gpu(n, u, code):
     with pytest.raises(pm.MertensError) as ei:
         pm.mertens_plan([n], u)
     assert ei.value.code == code
+
+
+@pytest.mark.parametrize("n,u", [
+    (2**63, 2**63 // 5),
+    (2**64 + 12345, (2**64 + 12345) // 7),
+    (10**20, 10**20 // 1000),
+    (11609864264058592345, 11609864264058592345 // 3000),
+])
+def test_describe_two_word_targets(n, u):
+    """Closed-form term counts for targets at and above 2^63, recomputed here
+    with Python integers (k = n // x, s = isqrt(k))."""
+    info = pm.mertens_describe(n, u)
+    X = n // u
+    assert info["n"] == n and info["X"] == X
+    d = g = 0
+    for x in range(1, X + 1):
+        k = n // x
+        s = math.isqrt(k)
+        d += s
+        g += max(0, k // (s + 1) - (X // x + 1) + 1)
+    assert (info["direct_terms"], info["gathered_terms"]) == (d, g)
+    assert info["y_max"] == max(math.isqrt(n), n // (X + 1))
 
 
 def test_server_without_usable_device_fails_cleanly():

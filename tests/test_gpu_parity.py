@@ -271,6 +271,54 @@ def test_batch_of_close_targets_1e17(table1):
         assert res[i][1][X - 1] == oracle.mertens(ns[i] // X, L=10**8), i
 
 
+# ---- two-word entries (k >= 2^63) ----------------------------------------------
+# MERTENS_WIDE_FROM moves the bound above which an entry takes the two-word
+# kernel, so that kernel can be compared with the oracle where the oracle is
+# cheap: first on every entry (k >= 2) of small targets, then on the first
+# entries of n ~ 10^12.
+
+def test_two_word_kernel_on_every_entry_small_n(monkeypatch):
+    monkeypatch.setenv("MERTENS_WIDE_FROM", "2")
+    M = oracle.mertens_table(2000)
+    for n in range(1, 121, 2):
+        us = [1] if n == 1 else range(math.isqrt(n) + 1, n + 1)
+        for u in us:
+            m, arr = gpu_array(n, u)
+            x = np.arange(1, n // u + 1)
+            assert m == M[n]
+            assert np.array_equal(arr, M[n // x].astype(np.int64)), (n, u)
+        m, arr = gpu_array(n, 0, 3)   # blocks of 3 y
+        assert m == M[n], n
+
+
+@pytest.mark.parametrize("n,u,bl,wide_from", [
+    (10**12 + 12345, 10**8, 2**24, 10**11),      # x <= 10 two-word
+    (10**12 - 1, 3 * 10**7, 2**20, 2 * 10**9),   # x <= 499, short blocks
+    (999_999_999_989, 0, 0, 10**6),              # every entry but the last ones
+])
+def test_two_word_kernel_matches_oracle(n, u, bl, wide_from, monkeypatch):
+    ref_m, ref_arr = gpu_array(n, u, bl)
+    monkeypatch.setenv("MERTENS_WIDE_FROM", str(wide_from))
+    m, arr = gpu_array(n, u, bl)
+    assert m == ref_m and np.array_equal(arr, ref_arr)
+    assert np.array_equal(arr, oracle.mertens_array(n, len(arr), L=10**8))
+
+
+@pytest.mark.parametrize("n", [11609864264058592345, 10**19])
+def test_two_word_targets_paper_values(n, table1):
+    """Sec. 5 Table 1 and Sec. 6: M(10^19) and the new extreme value, both
+    above 2^63 (entry x = 1 takes the two-word kernel)."""
+    m, arr = gpu_array(n)
+    assert m == table1[n]
+    # the entries with the smallest k, by the oracle recursion
+    X = len(arr)
+    for x in (X, X - 1, X - 1000):
+        assert arr[x - 1] == oracle.mertens(n // x, L=2 * 10**7), x
+    # entry x = 2 (k = floor(n/2) < 2^63) equals a separate one-word run
+    m2, _ = gpu_array(n // 2)
+    assert arr[1] == m2
+
+
 # ---- full size: n = 10^16, u = 4e10, block 2^28 ------------------------------
 
 def test_table1_1e16_full_configuration(table1):
