@@ -38,13 +38,13 @@ constexpr uint32_t kPatternPeriod = 44100;
 constexpr uint32_t kPatternWords = kPatternPeriod / 2;
 
 // Byte sieve (the fast variant of a1 + a2): one byte per y holding the sum of
-// odd weights w(p) = the odd integer nearest 4 log2 p (so its parity is the
+// odd weights w(p) = the odd integer nearest S log2 p (so its parity is the
 // parity of the prime count), and one bit per y set when a prime square
-// divides y.  A tile of kByteTile y takes 128 KiB + 16 KiB of shared memory.
+// divides y.  S = 4 while y < 2^42, else 3 (up to 2^54).  A tile of kByteTile
+// y takes 128 KiB + 16 KiB of shared memory.
 constexpr int kByteTile = 131072;
 constexpr int kByteWords = kByteTile / 4;
 constexpr int kByteSqWords = kByteTile / 32;
-constexpr int kByteScale = 4;
 // Pre-sieve tables of the byte sieve: 16 copies of the byte pattern of
 // 2, 3, 5, 7, copy k starting at phase k, each long enough for any phase plus
 // one tile (so a tile is one 16-byte aligned copy), and the square flags of

@@ -32,7 +32,8 @@ struct PrimeTable {
     uint32_t *blk_qm = nullptr;   // per block: floor(y1 / p) mod p
     uint32_t *pat_even = nullptr; // pre-sieve pattern words for an even phase
     uint32_t *pat_odd = nullptr;  // ... and for an odd phase
-    // byte sieve (null when the table was built without it)
+    // byte sieve (null when the table was built without it), weight scale S
+    uint32_t byte_scale = 0;
     uint4 *pq = nullptr;          // {p, m32(p), m32(p^2) or 0, s(p) | s(p^2) << 8 | w(p) << 16}
     uint64_t *blk_r2 = nullptr;   // per block: y1 mod p^2
     uint4 *pat8 = nullptr;        // 16 phase copies of the byte pattern

@@ -284,18 +284,21 @@ __global__ void __launch_bounds__(kSieveThreads, 1) mu_sieve_kernel(SieveArgs a)
 // invariant-divisor multiply; and the decode works on four y per 32-bit word.
 //
 // Byte of y: B0 + sum over the distinct sieving primes p | y of w(p), where
-// w(p) is the odd integer nearest 4 log2 p (|w(p) - 4 log2 p| <= 1) and B0 a
-// bias fixed per tile.  Because every weight is odd, the parity of the sum is
-// the parity of the prime count.  For squarefree y with unsieved cofactor c
-// (1 or a prime > P, as in the 16-bit kernel) the weight sum A satisfies
-//     c = 1:  A >= 4 log2 y - E,     c > 1:  A <= 4 log2 y - 4 log2 P + E,
-// E <= 11 the summed rounding error (y < 2^42 has at most 11 distinct prime
-// factors).  With P >= 2^10 the threshold T = 4 log2 y - 2 log2 P separates
-// the two with >= 9 units either side, so an integer threshold anywhere in
-// [T - 2, T] is exact; tiles at y >= 2^26 use one even threshold thr per tile
-// and B0 = 127 - thr (odd), which puts the decision into bit 7 of the byte
-// and the count parity (xor 1) into bit 0:  mu = -1 exactly when bit 0 and
-// bit 7 of the biased byte differ.  Bytes stay below 2^8 (A + B0 <= 182).
+// w(p) is the odd integer nearest S log2 p (|w(p) - S log2 p| <= 1; S = 4
+// below 2^42, 3 above) and B0 a bias fixed per tile.  Because every weight is
+// odd, the parity of the sum is the parity of the prime count.  For
+// squarefree y with unsieved cofactor c (1 or a prime > P, as in the 16-bit
+// kernel) the weight sum A satisfies
+//     c = 1:  A >= S log2 y - E,     c > 1:  A <= S log2 y - S log2 P + E,
+// E the summed rounding error, at most the number of distinct prime factors
+// (11 below 2^42, 13 below 2^54).  The threshold T = S log2 y - (S/2) log2 P
+// separates the two with (S/2) log2 P - E units either side; the host takes
+// this kernel only where that exceeds 2.5 (P >= 2^10), so an integer
+// threshold anywhere in [T - 2, T] is exact.  Tiles at y >= 2^26 use one even
+// threshold thr per tile and B0 = 127 - thr (odd), which puts the decision
+// into bit 7 of the byte and the count parity (xor 1) into bit 0:  mu = -1
+// exactly when bit 0 and bit 7 of the biased byte differ.  The host also
+// keeps thr < 127 and the biased bytes below 2^8.
 // ---------------------------------------------------------------------------
 struct ByteArgs {
     uint64_t y1;
@@ -303,7 +306,8 @@ struct ByteArgs {
     uint32_t np;          // primes used (all p <= P)
     uint32_t np_piece;    // [4, np_piece): p < 128, sieved in eighth-tile pieces
     uint32_t np_small;    // [np_piece, np_small): p < 2048, a warp per prime
-    float thr_half;       // 2 log2 P
+    float scale;          // S: w(p) = odd integer nearest S log2 p
+    float thr_half;       // (S/2) log2 P
     const uint4 *pq;
     const uint32_t *r;    // y1 mod p
     const uint64_t *r2;   // y1 mod p^2
@@ -402,10 +406,10 @@ __device__ __forceinline__ void byte_large_prime(uint4 q, uint32_t r, uint64_t r
         atomicOr(&sq[(uint32_t)o2 >> 5], 1u << ((uint32_t)o2 & 31u));
 }
 
-// floor(4 log2 y - 2 log2 P) for one y (tiles below 2^26).
-__device__ __forceinline__ int byte_thr(uint64_t y, float thr_half)
+// floor(S log2 y - (S/2) log2 P) for one y (tiles below 2^26).
+__device__ __forceinline__ int byte_thr(uint64_t y, float scale, float thr_half)
 {
-    return (int)floorf((float)kByteScale * __log2f(__ull2float_rn(y)) - thr_half);
+    return (int)floorf(scale * __log2f(__ull2float_rn(y)) - thr_half);
 }
 
 __global__ void __launch_bounds__(kSieveThreads, 1) mu_sieve_byte_kernel(ByteArgs a)
@@ -483,7 +487,7 @@ __global__ void __launch_bounds__(kSieveThreads, 1) mu_sieve_byte_kernel(ByteArg
     const bool tile_thr = t1 >= kByteTileThrMin;
     uint32_t bias4 = 0;
     if (tile_thr) {
-        int thr = (int)floorf((float)kByteScale * log2f(__ull2float_rn(t1)) - a.thr_half);
+        int thr = (int)floorf(a.scale * log2f(__ull2float_rn(t1)) - a.thr_half);
         thr &= ~1;
         bias4 = (uint32_t)(127 - thr) * 0x01010101u;
     }
@@ -515,7 +519,7 @@ __global__ void __launch_bounds__(kSieveThreads, 1) mu_sieve_byte_kernel(ByteArg
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         const uint32_t A = (ws[k] >> (8 * j)) & 255u;
-                        const int th = byte_thr(t1 + o0 + 4 * k + j, a.thr_half);
+                        const int th = byte_thr(t1 + o0 + 4 * k + j, a.scale, a.thr_half);
                         // count parity xor [c > 1]
                         const uint32_t bit = (A & 1u) ^ ((int)A > th ? 0u : 1u);
                         neg |= bit << (8 * j);
@@ -646,10 +650,10 @@ static uint64_t isqrt_u64(uint64_t v)
     return r;
 }
 
-// Odd integer nearest kByteScale * log2 p (ties upward).
-static uint32_t byte_weight(uint32_t p)
+// Odd integer nearest S log2 p (ties upward).
+static uint32_t byte_weight(uint32_t p, uint32_t S)
 {
-    const double x = kByteScale * std::log2((double)p);
+    const double x = S * std::log2((double)p);
     return 2u * (uint32_t)std::floor((x - 1.0) / 2.0 + 0.5) + 1u;
 }
 
@@ -664,12 +668,12 @@ static int byte_tables_create(PrimeTable *t, const std::vector<uint32_t> &pr, cu
         const uint32_t m1 = magic32_of(p, &s1);
         const uint64_t p2 = (uint64_t)p * p;
         const uint32_t m2 = p2 < (1ull << 30) ? magic32_of((uint32_t)p2, &s2) : 0u;
-        pq[i] = make_uint4(p, m1, m2, s1 | (s2 << 8) | (byte_weight(p) << 16));
+        pq[i] = make_uint4(p, m1, m2, s1 | (s2 << 8) | (byte_weight(p, t->byte_scale) << 16));
     }
     uint32_t w[4];
     const uint32_t small[4] = {2, 3, 5, 7};
     for (int q = 0; q < 4; ++q)
-        w[q] = byte_weight(small[q]);
+        w[q] = byte_weight(small[q], t->byte_scale);
     std::vector<uint8_t> pat(kPatternPeriod);
     std::vector<uint8_t> sqp(kPatternPeriod);
     for (uint32_t i = 0; i < kPatternPeriod; ++i) {
@@ -767,8 +771,11 @@ int prime_table_create(PrimeTable *t, const Allocator &al, uint64_t y_max, cudaS
     cudaMemcpyAsync(t->pat_odd, po.data(), kPatternWords * 4, cudaMemcpyHostToDevice, s);
     if (cudaStreamSynchronize(s) != cudaSuccess)
         return 3;
-    if (with_bytes)
+    // byte sieve tables: weight scale 4 below 2^42, 3 up to 2^54
+    if (with_bytes && y_max < (1ull << 54)) {
+        t->byte_scale = y_max < (1ull << 42) ? 4u : 3u;
         return byte_tables_create(t, pr, s);
+    }
     return 0;
 }
 
@@ -804,16 +811,34 @@ uint32_t prime_count_upto(const PrimeTable *t, uint64_t b)
     return lo;
 }
 
-// The byte kernel is exact when all primes up to P >= 2^10 are sieved, y stays
-// below 2^42 (at most 11 distinct prime factors, bytes below 2^8) and the
-// tile threshold 4 log2 y - 2 log2 P stays below 127 (bias B0 >= 0); blocks of
+// Most distinct prime factors of any y' <= y (primorials).
+static int omega_max(uint64_t y)
+{
+    static const uint64_t prim[15] = {2ull, 6ull, 30ull, 210ull, 2310ull, 30030ull, 510510ull,
+                                      9699690ull, 223092870ull, 6469693230ull,
+                                      200560490130ull, 7420738134810ull, 304250263527210ull,
+                                      13082761331670030ull, 614889782588491410ull};
+    int w = 0;
+    while (w < 15 && prim[w] <= y)
+        ++w;
+    return w;
+}
+
+// The byte kernel is exact when all primes up to P >= 2^10 are sieved and,
+// with E = the most distinct prime factors below y2 (the summed rounding
+// error of the weights), the half gap (S/2) log2 P exceeds E + 2 (the tile
+// threshold may sit up to 2 units low), the threshold S log2 y - (S/2) log2 P
+// stays below 127 (bias B0 >= 0) and biased bytes stay below 2^8.  Blocks of
 // at most 2^30 y keep its offsets within 31 bits.
 static bool byte_path_ok(const PrimeTable *t, uint64_t y2, uint64_t P, uint64_t len)
 {
-    if (!t->pq || P < 1024 || y2 >= (1ull << 42) || len > (1ull << 30))
+    if (!t->pq || P < 1024 || y2 >= (1ull << 54) || len > (1ull << 30))
         return false;
-    const double thr = kByteScale * std::log2((double)y2) - 2.0 * std::log2((double)P);
-    return thr < 126.0;
+    const double S = t->byte_scale;
+    const double half = 0.5 * S * std::log2((double)P);
+    const int E = omega_max(y2);
+    const double thr = S * std::log2((double)y2) - half;
+    return half >= E + 2.5 && thr < 126.0 && 127.0 + half + E + 3.0 < 255.0;
 }
 
 int sieve_block_enqueue(const PrimeTable *t, const SieveLaunch &L, cudaStream_t s)
@@ -847,7 +872,8 @@ int sieve_block_enqueue(const PrimeTable *t, const SieveLaunch &L, cudaStream_t 
         b.np_small = np_small < np ? np_small : np;
         const uint32_t np_p = prime_count_upto(t, 127);
         b.np_piece = np_p < b.np_small ? np_p : b.np_small;
-        b.thr_half = (float)(2.0 * std::log2((double)P));
+        b.scale = (float)t->byte_scale;
+        b.thr_half = (float)(0.5 * t->byte_scale * std::log2((double)P));
         b.pq = t->pq;
         b.r = t->blk_r;
         b.r2 = t->blk_r2;

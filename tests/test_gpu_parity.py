@@ -56,6 +56,9 @@ def gpu_array(n, u=0, block_len=0):
     (2**41 + 12345, 2 * BYTE_TILE + 7),
     (2**42 - BYTE_TILE - 77, BYTE_TILE + 70),
     (2**42 + 5, 1000),
+    # weight scale 3 above 2^42
+    (10**13 + 12345, 2 * BYTE_TILE + 9),
+    (2**47 + 999, BYTE_TILE + 5),
 ])
 def test_sieve_mu_matches_oracle(y1, length):
     mu = torch.empty(length + 16, dtype=torch.int8, device="cuda")
@@ -302,6 +305,16 @@ def test_two_word_kernel_matches_oracle(n, u, bl, wide_from, monkeypatch):
     m, arr = gpu_array(n, u, bl)
     assert m == ref_m and np.array_equal(arr, ref_arr)
     assert np.array_equal(arr, oracle.mertens_array(n, len(arr), L=10**8))
+
+
+def test_two_word_target_1e20(table1):
+    """Sec. 5 Table 1: M(10^20); entries x <= 10 take the two-word kernel and
+    the sieve runs to ~10^13 (byte sieve at weight scale 3)."""
+    n = 10**20
+    m, arr = gpu_array(n)
+    assert m == table1[n] == 461113106
+    X = len(arr)
+    assert arr[X - 1] == oracle.mertens(n // X, L=2 * 10**7)
 
 
 @pytest.mark.parametrize("n", [11609864264058592345, 10**19])
