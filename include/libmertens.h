@@ -97,6 +97,35 @@ int mertens_plan(mertens_plan_t *out, const mertens_u128 *n, size_t count,
                  mertens_u128 u, uint64_t block_len);
 
 /*
+ * mertens_plan_window -- like mertens_plan, but the run covers only the sieve
+ * blocks of y in [y_first, y_last] (clipped to the targets' largest y) and
+ * stops before resolve.  Every contribution of the window to entry x's sum
+ * S[x] is affine in the window's unknown carry C = M(y_first - 1): direct and
+ * gathered terms are sums of M(y) = M_loc(y) + C, with M_loc the prefix sum
+ * of mu from y_first (Sec. 2-3; the paper has no window form, this is the
+ * decomposition that lets windows run in any order or on several devices).
+ * The run computes S_loc (C taken as 0); the plan also knows coef[x], the
+ * coefficient of C, so the window adds S_loc[x] + C coef[x] (mod 2^64).
+ * Windows that partition [1, y_max], each with its carry, sum to the S of a
+ * whole run; resolve is then M[x] = 1 - S[x] - sum_{j>=2} M[xj].
+ * Errors: those of mertens_plan; MERTENS_EINVAL when y_first = 0 or
+ * y_last < y_first.  mertens_result on a window plan is MERTENS_EINVAL.
+ */
+int mertens_plan_window(mertens_plan_t *out, const mertens_u128 *n, size_t count,
+                        mertens_u128 u, uint64_t block_len, uint64_t y_first, uint64_t y_last);
+
+/*
+ * mertens_window_result -- wait for the last run of window plan `plan` and
+ * return target i's partial sums: S_loc[x-1] and coef[x-1] for
+ * x = 1..min(cap, X_i) (either may be NULL; uint64, mod 2^64), *len = X_i,
+ * and *mu_sum = M(y_last) - M(y_first - 1), the carry the next window adds.
+ * Errors: MERTENS_EINVAL (not a window plan, bad i), MERTENS_ENOTREADY,
+ * MERTENS_ECUDA.
+ */
+int mertens_window_result(mertens_plan_t plan, size_t i, uint64_t *S_loc, uint64_t *coef,
+                          size_t cap, size_t *len, int64_t *mu_sum);
+
+/*
  * mertens_run -- enqueue the whole computation on `stream`: for every sieve
  * block, mu_sieve (segmented Moebius sieve, Sec. 3), m_scan (M(y) by prefix
  * sum with the carry of the previous block), mertens_update (every array

@@ -59,7 +59,7 @@ EXPORTS = [
     "mertens_set_tuning", "mertens_get_tuning", "mertens_autotune",
     "mertens_server_create", "mertens_server_submit", "mertens_server_poll",
     "mertens_server_wait", "mertens_server_times", "mertens_server_stats_get",
-    "mertens_server_destroy",
+    "mertens_server_destroy", "mertens_plan_window", "mertens_window_result",
 ]
 
 
@@ -102,6 +102,12 @@ def load():
         lib.mertens_plan.argtypes = [ctypes.POINTER(P), ctypes.POINTER(mertens_u128), sz,
                                      mertens_u128, u64]
         lib.mertens_plan.restype = c_int
+        lib.mertens_plan_window.argtypes = [ctypes.POINTER(P), ctypes.POINTER(mertens_u128), sz,
+                                            mertens_u128, u64, u64, u64]
+        lib.mertens_plan_window.restype = c_int
+        lib.mertens_window_result.argtypes = [P, sz, P, P, sz, ctypes.POINTER(sz),
+                                              ctypes.POINTER(i64)]
+        lib.mertens_window_result.restype = c_int
         lib.mertens_run.argtypes = [P, P]
         lib.mertens_run.restype = c_int
         lib.mertens_result.argtypes = [P, sz, ctypes.POINTER(i64), P, sz,
@@ -204,6 +210,33 @@ def mertens_plan(n, u: int = 0, block_len: int = 0) -> int:
     _check(lib.mertens_plan(ctypes.byref(h), arr, len(ns), u128(u), int(block_len)),
            "mertens_plan")
     return int(h.value)
+
+
+def mertens_plan_window(n, y_first: int, y_last: int, u: int = 0, block_len: int = 0) -> int:
+    """A plan that runs only the sieve blocks of y in [y_first, y_last] (no
+    resolve); read it with mertens_window_result."""
+    lib = load()
+    ns = [int(n)] if isinstance(n, (int, np.integer)) else [int(v) for v in n]
+    arr = (mertens_u128 * len(ns))(*[u128(v) for v in ns])
+    h = ctypes.c_void_p()
+    _check(lib.mertens_plan_window(ctypes.byref(h), arr, len(ns), u128(u), int(block_len),
+                                   int(y_first), int(y_last)), "mertens_plan_window")
+    return int(h.value)
+
+
+def mertens_window_result(plan: int, i: int = 0):
+    """(S_loc, coef, mu_sum) of target i of a window plan: the window adds
+    S_loc + C * coef (uint64 arrays, mod 2^64) to the entries' sums, C =
+    M(y_first - 1); mu_sum = M(y_last) - M(y_first - 1)."""
+    lib = load()
+    X = mertens_plan_info(plan, i)["X"]
+    S = np.zeros(X, dtype=np.uint64)
+    c = np.zeros(X, dtype=np.uint64)
+    ln = ctypes.c_size_t()
+    mu = ctypes.c_int64()
+    _check(lib.mertens_window_result(plan, i, S.ctypes.data, c.ctypes.data, X, ctypes.byref(ln),
+                                     ctypes.byref(mu)), "mertens_window_result")
+    return S, c, int(mu.value)
 
 
 def mertens_run(plan: int, stream=None) -> None:

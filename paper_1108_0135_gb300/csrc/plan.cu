@@ -171,6 +171,12 @@ struct mertens_plan_s {
     std::vector<uint64_t> direct, gathered, ymax_q;
     uint64_t nent = 0;
     uint64_t y_max = 0, block_len = 0, nblocks = 0, ydense = 0, jmax = 0, mg_n = 0;
+    // sieved range: [1, y_max] for a whole run; a window plan runs only the
+    // blocks of [y_first, y_last], with M(y_first - 1) taken as 0, and returns
+    // per entry S_loc and the coefficient of that carry (coef)
+    uint64_t y_first = 1, y_last = 0;
+    bool window = false;
+    std::vector<uint64_t> coef;
     mertens_tuning tuning{};
     uint64_t terms = 0, dense_y = 0, gather_j = 0;
     double sieve_updates = 0;
@@ -235,6 +241,13 @@ struct mertens_plan_s {
         return (T *)p;
     }
 };
+
+// y range of block b of a plan.
+static void block_range(const mertens_plan_s *p, uint64_t b, uint64_t *y1, uint64_t *y2)
+{
+    *y1 = p->y_first + b * p->block_len;
+    *y2 = std::min(*y1 + p->block_len - 1, p->y_last);
+}
 
 // Tuning in force for new plans (mertens_set_tuning); MERTENS_* environment
 // variables override single fields for experiments.
@@ -406,7 +419,8 @@ int mertens_describe(mertens_u128 n, mertens_u128 u, mertens_query_info *info)
 }
 
 static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count, mertens_u128 u,
-                       uint64_t block_len, const mertens_tuning &tn)
+                       uint64_t block_len, const mertens_tuning &tn, bool window = false,
+                       uint64_t w_first = 1, uint64_t w_last = UINT64_MAX)
 {
     if (!out)
         return MERTENS_EINVAL;
@@ -574,13 +588,17 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
         delete p;
         return MERTENS_ENOTSUP;
     }
+    p->window = window;
+    p->y_first = window ? w_first : 1;
+    p->y_last = window ? std::min(w_last, p->y_max) : p->y_max;
+    const uint64_t span = p->y_last >= p->y_first ? p->y_last - p->y_first + 1 : 0;
     if (block_len == 0) {
         // one block when it fits 2^28 y, else 2^28 (up to 2^36 y) or 2^30 y blocks
-        uint64_t cap = p->y_max > (1ull << 36) ? (1ull << 30) : (1ull << 28);
+        uint64_t cap = p->y_last > (1ull << 36) ? (1ull << 30) : (1ull << 28);
         if (tn.block_cap >= kSieveTile && tn.block_cap <= (1ull << 31))
             cap = tn.block_cap;
-        block_len = std::min<uint64_t>(((p->y_max + kSieveTile - 1) / kSieveTile) * kSieveTile,
-                                       cap);
+        block_len = std::max<uint64_t>(
+            1, std::min<uint64_t>(((span + kSieveTile - 1) / kSieveTile) * kSieveTile, cap));
     }
     if (block_len > (1ull << 31)) {
         set_last_error("mertens_plan: block_len must be <= 2^31");
@@ -588,7 +606,16 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
         return MERTENS_EINVAL;
     }
     p->block_len = block_len;
-    p->nblocks = (p->y_max + block_len - 1) / block_len;
+    p->nblocks = (span + block_len - 1) / block_len;
+    if (window) {
+        // only the window's part of the dense list, and divisor magics for
+        // the j whose quotient can reach the window
+        p->ydense = p->y_first <= p->ydense ? std::min(p->ydense, p->y_last) : 0;
+        p->jmax = 0;
+        for (size_t e = 0; e < K.size(); ++e)
+            if (K[e])
+                p->jmax = std::max(p->jmax, std::min(JC0[e], K[e] / p->y_first));
+    }
     p->mg_n = std::max(p->jmax, p->ydense) + 1;
 
     // ---- dense work items: groups sorted by cut-off, chunk ranges ----
@@ -662,8 +689,8 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
     std::vector<GatherItem> gitems;
     std::vector<std::pair<uint64_t, uint64_t>> ranges;
     for (uint64_t b = 0; b < p->nblocks; ++b) {
-        const uint64_t y1 = 1 + b * block_len;
-        const uint64_t y2 = std::min(y1 + block_len - 1, p->y_max);
+        uint64_t y1, y2;
+        block_range(p, b, &y1, &y2);
         p->gblk.push_back((uint32_t)gitems.size());
         const uint64_t end = std::min(y2, p->gather_smem_end);
         p->gend.push_back(y1 <= end ? end : y1 - 1);
@@ -730,8 +757,8 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
     if (!p->wide.empty()) {
         p->wide_grid.assign(p->nblocks, 0);
         for (uint64_t b = 0; b < p->nblocks; ++b) {
-            const uint64_t y1 = 1 + b * block_len;
-            const uint64_t y2 = std::min(y1 + block_len - 1, p->y_max);
+            uint64_t y1, y2;
+            block_range(p, b, &y1, &y2);
             uint64_t most = 0;
             for (const WideEntry &W : p->wide) {
                 uint64_t nd, ja, ng;
@@ -739,6 +766,40 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
                 most = std::max(most, nd + ng);
             }
             p->wide_grid[b] = (uint32_t)((most + kWideUnitsPerCta - 1) / kWideUnitsPerCta);
+        }
+    }
+
+    // ---- window plans: coefficient of the carry M(y_first - 1) per entry ----
+    // gathered terms: one per j with floor(k/j) in the window; the dense
+    // form's boundary term -M(yc) floor(k/(yc+1)) when yc is in it; direct
+    // terms of two-word entries: sum of floor(k/y) - floor(k/(y+1)) over the
+    // window's y <= s, which telescopes.
+    if (window) {
+        const uint64_t a = p->y_first, z = p->y_last;
+        p->coef.assign(K.size(), 0);
+        if (z >= a) {
+            for (size_t e = 0; e < K.size(); ++e) {
+                const uint64_t k = K[e];
+                if (k == 0)
+                    continue;
+                const uint64_t jb = std::max(JLO[e], k / (z + 1) + 1);
+                const uint64_t jt = std::min(JC0[e], k / a);
+                uint64_t c = jt >= jb ? jt - jb + 1 : 0;
+                if (YCE[e] >= a && YCE[e] <= z)
+                    c -= JC0[e];
+                p->coef[e] = c;
+            }
+            for (const WideEntry &W : p->wide) {
+                const u128 k = ((u128)W.k_hi << 64) | W.k_lo;
+                uint64_t c = 0;
+                const uint64_t dl = std::min(z, W.s);
+                if (a <= dl)
+                    c += (uint64_t)(k / a) - (uint64_t)(k / ((u128)dl + 1));
+                uint64_t nd, ja, ng;
+                wide_ranges(W, a, z, &nd, &ja, &ng);
+                c += ng;
+                p->coef[W.e] = c;
+            }
         }
     }
 
@@ -807,7 +868,7 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
     if (any_null)
         rc = MERTENS_ENOMEM;
     if (rc == MERTENS_OK) {
-        int prc = prime_table_create(&p->pt, p->al, p->y_max, nullptr);
+        int prc = prime_table_create(&p->pt, p->al, std::max<uint64_t>(p->y_last, 1), nullptr);
         if (prc != 0)
             rc = prc == 6 ? MERTENS_ENOTSUP : (prc == 2 ? MERTENS_ENOMEM : MERTENS_ECUDA);
     }
@@ -820,8 +881,8 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
             pre[i + 1] = pre[i] + 1.0 / q + 1.0 / (q * q);
         }
         for (uint64_t b = 0; b < p->nblocks; ++b) {
-            const uint64_t y1 = 1 + b * block_len;
-            const uint64_t y2 = std::min(y1 + block_len - 1, p->y_max);
+            uint64_t y1, y2;
+            block_range(p, b, &y1, &y2);
             const uint64_t P = std::max<uint64_t>(7, isqrt64(y2));
             p->sieve_updates += (double)(y2 - y1 + 1) * pre[prime_count_upto(&p->pt, P)];
         }
@@ -984,6 +1045,8 @@ static int run_enqueue(mertens_plan_s *p, cudaStream_t origin, uint64_t *out)
     cudaMemcpyAsync(p->dJCUR, p->dJC0, E * 8, cudaMemcpyDeviceToDevice, su);
     cudaMemsetAsync(p->dcarry, 0, 8 * (p->nblocks + 1), ss);
     cudaMemsetAsync(p->derr, 0, 4, su);
+    if (p->window && p->y_first <= p->ydense)
+        cudaMemsetAsync(p->dmu_aux, 0, p->ydense + 1, ss);  // mu outside the window: none
     if (!p->mg_built) {
         r = magic_table_enqueue(p->dMG, p->mg_n, su);
         if (r < 0)
@@ -997,10 +1060,13 @@ static int run_enqueue(mertens_plan_s *p, cudaStream_t origin, uint64_t *out)
         cudaStreamWaitEvent(sd, p->ev_reset, 0);
     }
     {
-        bool dense_done = false;
+        // the dense part runs once mu is known up to Y_dense (or up to the
+        // window's end); a window above Y_dense has none
+        bool dense_done = p->y_first > p->ydense;
+        const uint64_t dense_at = std::min(p->ydense, p->y_last);
         for (uint64_t b = 0; b < p->nblocks; ++b) {
-            const uint64_t y1 = 1 + b * p->block_len;
-            const uint64_t y2 = std::min(y1 + p->block_len - 1, p->y_max);
+            uint64_t y1, y2;
+            block_range(p, b, &y1, &y2);
             const int buf = (int)(b & 1);
             if (!serial && b >= 2)
                 cudaStreamWaitEvent(ss, p->ev_upd[b - 2], 0);
@@ -1036,7 +1102,7 @@ static int run_enqueue(mertens_plan_s *p, cudaStream_t origin, uint64_t *out)
             launches += r;
             if (!serial)
                 cudaEventRecord(p->ev_sieved[b], ss);
-            if (!dense_done && y2 >= p->ydense) {
+            if (!dense_done && y2 >= dense_at) {
                 s = sd;
                 if (!serial)
                     cudaStreamWaitEvent(sd, p->ev_sieved[b], 0);
@@ -1147,13 +1213,15 @@ static int run_enqueue(mertens_plan_s *p, cudaStream_t origin, uint64_t *out)
             cudaEventRecord(p->ev_sieve_done, ss);
             cudaStreamWaitEvent(su, p->ev_sieve_done, 0);
         }
-        PhaseEvents pe;
-        ev_begin(p, kPhResolve, su, &pe);
-        r = resolve_enqueue(p->dqs, (uint32_t)p->nq, p->dS, p->dK, p->dR, su);
-        ev_end(p, su, &pe);
-        if (r < 0)
-            goto fail;
-        launches += r;
+        if (!p->window) {
+            PhaseEvents pe;
+            ev_begin(p, kPhResolve, su, &pe);
+            r = resolve_enqueue(p->dqs, (uint32_t)p->nq, p->dS, p->dK, p->dR, su);
+            ev_end(p, su, &pe);
+            if (r < 0)
+                goto fail;
+            launches += r;
+        }
         if (!serial) {
             cudaEventRecord(p->ev_join, su);
             cudaStreamWaitEvent(origin, p->ev_join, 0);
@@ -1251,6 +1319,11 @@ int mertens_result(mertens_plan_t p, size_t i, int64_t *M_n, int64_t *entries, s
         set_last_error("mertens_result: %s", cudaGetErrorString(cudaGetLastError()));
         return MERTENS_ECUDA;
     }
+    if (p->window) {
+        set_last_error("mertens_result: a window plan has partial sums only "
+                       "(mertens_window_result)");
+        return MERTENS_EINVAL;
+    }
     uint32_t err = 0;
     if (cudaMemcpy(&err, p->derr, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
         return MERTENS_ECUDA;
@@ -1271,6 +1344,53 @@ int mertens_result(mertens_plan_t p, size_t i, int64_t *M_n, int64_t *entries, s
         if (cudaMemcpy(entries, p->dR + o, m * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
             return MERTENS_ECUDA;
         p->d2h_bytes += m * 8;
+    }
+    return MERTENS_OK;
+}
+
+int mertens_plan_window(mertens_plan_t *out, const mertens_u128 *n, size_t count,
+                        mertens_u128 u, uint64_t block_len, uint64_t y_first, uint64_t y_last)
+{
+    if (out)
+        *out = nullptr;
+    if (y_first == 0 || y_last < y_first) {
+        set_last_error("mertens_plan_window: need 1 <= y_first <= y_last");
+        return MERTENS_EINVAL;
+    }
+    return plan_create(out, n, count, u, block_len, tuning_now(), true, y_first, y_last);
+}
+
+int mertens_window_result(mertens_plan_t p, size_t i, uint64_t *S_loc, uint64_t *coef,
+                          size_t cap, size_t *len, int64_t *mu_sum)
+{
+    if (!p || i >= p->nq || !p->window) {
+        set_last_error("mertens_window_result: bad plan, index, or not a window plan");
+        return MERTENS_EINVAL;
+    }
+    if (!p->ran) {
+        set_last_error("mertens_window_result: mertens_run was not called");
+        return MERTENS_ENOTREADY;
+    }
+    if (cudaEventSynchronize(p->done) != cudaSuccess) {
+        set_last_error("mertens_window_result: %s", cudaGetErrorString(cudaGetLastError()));
+        return MERTENS_ECUDA;
+    }
+    if (len)
+        *len = p->X[i];
+    const uint64_t o = p->off[i];
+    const size_t m = std::min<size_t>(cap, p->X[i]);
+    if (S_loc && m) {
+        if (cudaMemcpy(S_loc, p->dS + o, m * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return MERTENS_ECUDA;
+        p->d2h_bytes += m * 8;
+    }
+    if (coef && m)
+        memcpy(coef, p->coef.data() + o, m * 8);
+    if (mu_sum) {
+        *mu_sum = 0;
+        if (p->nblocks &&
+            cudaMemcpy(mu_sum, p->dcarry + p->nblocks, 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return MERTENS_ECUDA;
     }
     return MERTENS_OK;
 }
@@ -1343,7 +1463,7 @@ int mertens_run_stats_get(mertens_plan_t p, mertens_run_stats *st)
     if (cudaEventSynchronize(p->done) != cudaSuccess)
         return MERTENS_ECUDA;
     st->blocks = p->nblocks;
-    st->y_sieved = p->y_max;
+    st->y_sieved = p->y_last >= p->y_first ? p->y_last - p->y_first + 1 : 0;
     st->terms = p->terms;
     st->kernels = p->kernels;
     st->dense_y = p->dense_y;

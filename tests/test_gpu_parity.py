@@ -332,6 +332,85 @@ def test_two_word_targets_paper_values(n, table1):
     assert arr[1] == m2
 
 
+# ---- windows: contributions affine in the window's carry ------------------------
+
+def _resolve_host(n, S):
+    """M[x] = 1 - S[x] - sum_{j>=2} M[xj] (mod 2^64), x = X..1, read as int64."""
+    X = len(S)
+    R = [0] * (X + 1)
+    for x in range(X, 0, -1):
+        if n // x == 1:
+            R[x] = 1
+            continue
+        acc = sum(R[x * j] for j in range(2, X // x + 1))
+        R[x] = (1 - int(S[x - 1]) - acc) % 2**64
+    return np.array(R[1:], dtype=np.uint64).view(np.int64)
+
+
+def _windows_sum(n, u, cuts, block_lens):
+    """S of a whole run assembled from windows [cuts[i], cuts[i+1]-1], each
+    S_loc + C coef with C = M(window start - 1) chained from the mu sums."""
+    total = None
+    carry = 0
+    for (a, b), bl in zip(zip(cuts[:-1], cuts[1:]), block_lens):
+        plan = pm.mertens_plan_window([n], a, b - 1, u, bl)
+        try:
+            pm.mertens_run(plan)
+            S, coef, mu = pm.mertens_window_result(plan, 0)
+        finally:
+            pm.mertens_destroy(plan)
+        part = S + np.uint64(carry % 2**64) * coef   # wraps mod 2^64
+        total = part if total is None else total + part
+        carry += mu
+    return total
+
+
+@pytest.mark.parametrize("wide_from", [None, 10**11])
+def test_windows_partition_equals_whole_run(wide_from, monkeypatch):
+    if wide_from:
+        monkeypatch.setenv("MERTENS_WIDE_FROM", str(wide_from))
+    n, u = 10**12 + 12345, 10**8
+    m, arr = gpu_array(n, u, 2**22)
+    ymax = pm.mertens_describe(n, u)["y_max"]
+    # the first cut splits the dense part (y_c ~ 1.6 sqrt(k) <= 1.6e6)
+    cuts = [1, 700_001, 5_000_001, ymax + 1]
+    S = _windows_sum(n, u, cuts, [2**18, 2**20 + 3, 0])
+    got = _resolve_host(n, S)
+    assert np.array_equal(got, arr)
+    assert np.array_equal(got, oracle.mertens_array(n, n // u, L=10**8))
+
+
+def test_window_two_word_target_at_1e13():
+    """n = 10^20 with u ~ n^(2/3): four 2^22-y blocks from y = 10^13, against
+    carry-free sums from the oracle's mu window (entries x <= 10 are two-word)."""
+    n, u = 10**20, 21544346900318
+    y1, L = 10**13, 4 * 2**22
+    y2 = y1 + L - 1
+    plan = pm.mertens_plan_window([n], y1, y2, u, 2**22)
+    try:
+        pm.mertens_run(plan)
+        S, coef, mu = pm.mertens_window_result(plan, 0)
+    finally:
+        pm.mertens_destroy(plan)
+    Mloc = np.cumsum(oracle.mu_window(y1, L).astype(np.int64))
+    assert mu == int(Mloc[-1])
+    X = n // u
+    assert len(S) == X
+    want_S, want_c = {}, {}
+    for x in range(1, X + 1):
+        k = n // x
+        ja = max(X // x + 1, k // (y2 + 1) + 1)
+        jb = k // y1                          # below the dense cut-off and sqrt(k)
+        if jb < ja:
+            continue
+        want_c[x] = jb - ja + 1
+        want_S[x] = sum(int(Mloc[k // j - y1]) for j in range(ja, jb + 1)) % 2**64
+    got_c = {int(i) + 1: int(v) for i, v in enumerate(coef) if v}
+    got_S = {int(i) + 1: int(v) for i, v in enumerate(S) if v}
+    assert got_c == want_c
+    assert got_S == {x: v for x, v in want_S.items() if v}
+
+
 # ---- full size: n = 10^16, u = 4e10, block 2^28 ------------------------------
 
 def test_table1_1e16_full_configuration(table1):
