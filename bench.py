@@ -334,6 +334,8 @@ def run_native(args, world, rank, local):
                            "u": i18["u"], "X": i18["X"],
                            "update_terms_per_s": (i18["direct_terms"] + i18["gathered_terms"])
                            / t18}
+        extra["batch_64_close_1e17"] = batch_measure(stream)
+        extra["u128_window_1e20"] = window_measure(stream)
         extra["serving"] = serving_measure(args.serve_sample)
 
 
@@ -404,10 +406,71 @@ def run_native(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def _timed_run(plan, stream):
+    """Seconds of one warm mertens_run (CUDA events on the launching stream)."""
+    import torch
+    import paper_1108_0135_gb300 as pm
+    pm.mertens_run(plan, stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    pm.mertens_run(plan, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def batch_measure(stream):
+    """64 close targets 10^17 + i 10^9 in one plan (one sieve pass): wall time
+    and update terms/s; M(10^17) from Table 1 checked; one target alone (its
+    own u) timed beside it."""
+    import paper_1108_0135_gb300 as pm
+    from paper_1108_0135_gb300 import workloads
+    cfg = workloads.BATCH_1E17
+    ns = cfg["n"]
+    plan = pm.mertens_plan(ns, cfg["u"], 0)
+    infos = [pm.mertens_plan_info(plan, i) for i in range(len(ns))]
+    t = _timed_run(plan, stream)
+    m0, _ = pm.mertens_result(plan, 0)
+    pm.mertens_destroy(plan)
+    assert m0 == -21830254, m0
+    terms = sum(i["direct_terms"] + i["gathered_terms"] for i in infos)
+    p1 = pm.mertens_plan([ns[0]])
+    t1 = _timed_run(p1, stream)
+    pm.mertens_destroy(p1)
+    return {"targets": len(ns), "wall_time_s": t, "update_terms_per_s": terms / t,
+            "queries_per_s": len(ns) / t, "u": infos[0]["u"], "X_each": infos[0]["X"],
+            "M_n0": m0, "expected_table1": -21830254,
+            "one_target_alone_s": t1, "alone_x64_over_batch": 64 * t1 / t}
+
+
+def window_measure(stream):
+    """Two-word target n = 10^20 (u ~ n^(2/3)): the update of 64 sieve blocks of
+    2^28 y from y = 10^13 (window plan: carry left symbolic), y sieved/s and
+    entries scanned/s."""
+    import paper_1108_0135_gb300 as pm
+    from paper_1108_0135_gb300 import workloads
+    cfg = workloads.WINDOW_1E20
+    plan = pm.mertens_plan_window(cfg["n"], cfg["y_first"], cfg["y_last"], cfg["u"],
+                                  cfg["block_len"])
+    info = pm.mertens_plan_info(plan, 0)
+    t = _timed_run(plan, stream)
+    S, coef, mu = pm.mertens_window_result(plan, 0)
+    pm.mertens_destroy(plan)
+    ny = cfg["y_last"] - cfg["y_first"] + 1
+    terms = int(np.count_nonzero(coef))
+    gathered = int(coef.astype(np.uint64).sum(dtype=np.uint64))
+    return {"n": str(cfg["n"][0]), "u": cfg["u"], "X": info["X"], "y_first": cfg["y_first"],
+            "blocks": 64, "y": ny, "wall_time_s": t, "y_sieved_per_s": ny / t,
+            "entries_scanned_per_s": info["X"] * 64 / t, "gathered_terms": gathered,
+            "entries_with_terms": terms, "mu_sum": mu}
+
+
 # DRAM bytes (read + write) per launch from one ncu capture of the current
 # kernel (profiles/), or None when the kernel changed since the capture.
 TRAFFIC_PER_LAUNCH = {
-    "mu_sieve": None,                      # kernel changed since the last capture
+    "mu_sieve": 1.058e6 + 476.671e6,       # profiles/mu_sieve_byte_1e16.md (one 2^28-y block)
     "update_dense": 989.370e6 + 5.861e6,   # profiles/dense_update_1e16.md
     "update_gathered": 1670.806e6 + 56.108e6,  # profiles/gather_tile_1e16.md (first block)
 }

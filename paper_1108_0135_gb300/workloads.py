@@ -18,6 +18,11 @@ BATCH_1E17 = dict(name="batch 64 x (1e17 + i*1e9)", n=[10**17 + i * 10**9 for i 
                   u=0, block_len=1 << 28)
 # Single query n = 10^18 on the 64-bit path.
 SINGLE_1E18 = dict(name="single n=1e18", n=[10**18], u=0, block_len=1 << 28)
+# Two-word target n = 10^20 (u ~ n^(2/3)): a fixed window of 64 sieve blocks
+# of 2^28 y starting at y = 10^13.
+WINDOW_1E20 = dict(name="n=1e20 window of 64 x 2^28 y from y=1e13", n=[10**20],
+                   u=21544346900318, block_len=1 << 28, y_first=10**13,
+                   y_last=10**13 + 64 * (1 << 28) - 1)
 
 
 def random_small_cases(seed: int, count: int, n_max: int):
