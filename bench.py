@@ -232,6 +232,7 @@ def serving_measure(sample: int):
     continuous-batching server, closed loop (all submitted at once) and open
     loop (Poisson arrivals at 0.8 x the closed-loop rate), against the same
     queries run one plan each."""
+    import paper_1108_0135_gb300 as pm
     from paper_1108_0135_gb300 import serve, workloads
 
     _, ns = workloads.serving_stream(seed=20261203, count=10_000)
@@ -243,6 +244,24 @@ def serving_measure(sample: int):
     arr = np.cumsum(np.random.default_rng(20261203).exponential(1.0 / rate, size=len(ns)))
     opened = serve.run_stream(ns, arrivals_s=arr)
     assert opened["answers"] == one["answers"]
+    # the same stream with a resident M(y) table (y <= 2^34, sieved once and
+    # timed separately): batches run update + resolve only
+    import torch
+    t0 = time.perf_counter()
+    table = pm.mertens_table_create(1 << 34, 10**16)
+    torch.cuda.synchronize()
+    t_table = time.perf_counter() - t0
+    tinfo = pm.mertens_table_info(table)
+    try:
+        tab = serve.run_stream(ns, table=table)
+        assert tab["answers"] == one["answers"]
+        rate_t = 0.8 * tab["queries_per_s"]
+        arr_t = np.cumsum(np.random.default_rng(20261203).exponential(1.0 / rate_t,
+                                                                       size=len(ns)))
+        tab_open = serve.run_stream(ns, arrivals_s=arr_t, table=table)
+        assert tab_open["answers"] == one["answers"]
+    finally:
+        pm.mertens_table_destroy(table)
     return {
         "sample": f"first {len(ns)} of the seeded 10^4-query stream, n log-uniform in "
                   f"[1e10, 1e16]",
@@ -253,6 +272,15 @@ def serving_measure(sample: int):
         "open_loop": {"rate_qps": rate, "qps": opened["queries_per_s"],
                       "p50_s": opened["p50_s"], "p99_s": opened["p99_s"]},
         "batched_over_one_per_plan": closed["queries_per_s"] / one["queries_per_s"],
+        "resident_table": {
+            "y_max": tinfo["y_max"], "n_max": tinfo["n_max"], "device_bytes": tinfo["bytes"],
+            "build_s": t_table,
+            "closed_loop": {"qps": tab["queries_per_s"], "p50_s": tab["p50_s"],
+                            "p99_s": tab["p99_s"], "batches": tab["stats"]["batches"]},
+            "open_loop": {"rate_qps": rate_t, "qps": tab_open["queries_per_s"],
+                          "p50_s": tab_open["p50_s"], "p99_s": tab_open["p99_s"]},
+            "over_one_per_plan": tab["queries_per_s"] / one["queries_per_s"],
+        },
     }
 
 

@@ -78,8 +78,11 @@ int mertens_set_allocator(mertens_alloc_fn alloc, mertens_free_fn release, void 
  *              quotients (the paper, Sec. 5, uses 128-bit integers there);
  *              all others with one-word quotients.  Copied; the caller
  *              keeps ownership.
- *   u          sieve limit shared by all targets.  {0,0} = chosen per target
- *              by the library (see mertens_tuning).  Otherwise it must
+ *   u          sieve limit shared by all targets.  {0,0} = chosen by the
+ *              library: a batch limit ub = f (sum n)^(2/3) Neff^(-1/5),
+ *              Neff = sum n / max n (f from mertens_tuning), and per target
+ *              u_i = min(n_i, ub), raised above floor(sqrt(n_i)) where
+ *              needed; the sieve runs to the largest targets' need.  Otherwise it must
  *              satisfy floor(sqrt(n_i)) < u <= n_i for every i (u = 1 is
  *              allowed for n_i = 1), else MERTENS_EINVAL.  u < 2^64 (else
  *              MERTENS_ENOTSUP).  Each target's array has X_i = floor(n_i/u_i)
@@ -95,6 +98,38 @@ int mertens_set_allocator(mertens_alloc_fn alloc, mertens_free_fn release, void 
  */
 int mertens_plan(mertens_plan_t *out, const mertens_u128 *n, size_t count,
                  mertens_u128 u, uint64_t block_len);
+
+/*
+ * Resident M(y) table.  The sieve's output (steps a1 + a2: M(y) for
+ * 1 <= y <= y_max) is computed once and kept in device memory (about
+ * 2 bytes per y), together with what the update needs independently of the
+ * target for all n <= n_max (the divisor magics and the squarefree list of
+ * the dense form).  Plans made on it run only the update and resolve, with
+ * the sieve limit u as large as the table allows (u = min(n, y_max + 1); the
+ * update's terms fall as 1/sqrt(u)); a target n <= y_max is read from the
+ * table directly.  The paper sieves per target (Sec. 3); sharing one sieve
+ * between queries is what Sec. 2 allows for close targets, taken to every
+ * target the table covers.
+ *
+ *   mertens_table_create: 1 <= y_max < 2^40, 1 <= n_max < 2^127; sieves on
+ *     `stream` and returns when done.  The table lives on the current device
+ *     and owns its memory (allocated through the allocator hook).
+ *     Errors: MERTENS_EINVAL, MERTENS_ENOMEM, MERTENS_ECUDA.
+ *   mertens_table_info: y_max, n_max and the device bytes held (each output
+ *     may be NULL).  Errors: MERTENS_EINVAL (NULL table).
+ *   mertens_plan_on_table: as mertens_plan, on the table's device; u = {0,0}
+ *     picks min(n, y_max + 1) per target.  MERTENS_ENOTSUP when a target
+ *     exceeds n_max or needs y, dense cut-offs or divisors beyond the table
+ *     (for example when y_max + 1 <= sqrt(n)); block_len must be a multiple of
+ *     2048 (0: 2^30).  The table must outlive its plans.
+ *   mertens_table_destroy: waits for the device, then frees the table.
+ */
+typedef struct mertens_table_s *mertens_table_t;
+int mertens_table_create(mertens_table_t *out, uint64_t y_max, mertens_u128 n_max, void *stream);
+int mertens_table_info(mertens_table_t table, uint64_t *y_max, mertens_u128 *n_max, size_t *bytes);
+int mertens_plan_on_table(mertens_plan_t *out, mertens_table_t table, const mertens_u128 *n,
+                          size_t count, mertens_u128 u, uint64_t block_len);
+void mertens_table_destroy(mertens_table_t table);
 
 /*
  * mertens_plan_window -- like mertens_plan, but the run covers only the sieve
@@ -280,9 +315,10 @@ int mertens_autotune(const mertens_u128 *n, size_t count, int runs, mertens_tuni
 /*
  * A server owns one worker thread on `device`.  Queries are submitted from
  * any host thread and answered asynchronously.  The worker groups waiting
- * queries of the same magnitude (floor(log2(n)/2)) into batches of at most
- * `max_batch` targets -- one plan, one shared sieve pass per batch (Sec. 2:
- * close values share the sieve) -- and keeps up to `max_inflight` batches
+ * queries of the same magnitude class (floor(bitlength(n)/20)) into batches
+ * of at most `max_batch` targets -- one plan, one shared sieve pass per
+ * batch (Sec. 2: close values share the sieve; every target of a batch takes
+ * u = min(n, the batch's sieve limit)) -- and keeps up to `max_inflight` batches
  * running at once, each on its own stream, admitting a new batch whenever a
  * slot is free and its estimated device memory fits what is left of
  * `mem_budget_bytes`.  Queries that arrive while others run on the GPU are
@@ -291,7 +327,7 @@ int mertens_autotune(const mertens_u128 *n, size_t count, int runs, mertens_tuni
  *
  *   mertens_server_create: device >= 0; mem_budget_bytes = 0 means 80% of the
  *     free device memory; max_inflight 1..16 (0 = 4); max_batch 1..4096
- *     (0 = 64).  Errors: MERTENS_EINVAL, MERTENS_ECUDA, MERTENS_ENOMEM.
+ *     (0 = 128).  Errors: MERTENS_EINVAL, MERTENS_ECUDA, MERTENS_ENOMEM.
  *   mertens_server_submit: 1 <= n < 2^63 (else MERTENS_ENOTSUP / EINVAL);
  *     *ticket receives the query's id.
  *   mertens_server_poll: MERTENS_OK with *M_n set once the answer is there,
@@ -318,6 +354,15 @@ typedef struct {
 int mertens_server_create(mertens_server_t *out, int device, size_t mem_budget_bytes,
                           uint32_t max_inflight, uint32_t max_batch);
 int mertens_server_submit(mertens_server_t srv, mertens_u128 n, uint64_t *ticket);
+/*
+ * mertens_server_use_table: batches admitted from now on whose targets are all
+ * <= the table's n_max are planned on `table` (mertens_plan_on_table: no
+ * sieve; u = min(n, y_max + 1)); others, and any batch the table cannot
+ * serve, get ordinary plans.  NULL detaches.  The table must be on the
+ * server's device and outlive the server's use of it.
+ * Errors: MERTENS_EINVAL.
+ */
+int mertens_server_use_table(mertens_server_t srv, mertens_table_t table);
 int mertens_server_poll(mertens_server_t srv, uint64_t ticket, int64_t *M_n);
 int mertens_server_wait(mertens_server_t srv, uint64_t ticket, int64_t *M_n, double timeout_s);
 int mertens_server_times(mertens_server_t srv, uint64_t ticket, uint64_t *t_submit_ns,

@@ -60,6 +60,8 @@ EXPORTS = [
     "mertens_server_create", "mertens_server_submit", "mertens_server_poll",
     "mertens_server_wait", "mertens_server_times", "mertens_server_stats_get",
     "mertens_server_destroy", "mertens_plan_window", "mertens_window_result",
+    "mertens_table_create", "mertens_table_info", "mertens_plan_on_table", "mertens_table_destroy",
+    "mertens_server_use_table",
 ]
 
 
@@ -108,6 +110,18 @@ def load():
         lib.mertens_window_result.argtypes = [P, sz, P, P, sz, ctypes.POINTER(sz),
                                               ctypes.POINTER(i64)]
         lib.mertens_window_result.restype = c_int
+        lib.mertens_table_create.argtypes = [ctypes.POINTER(P), u64, mertens_u128, P]
+        lib.mertens_table_create.restype = c_int
+        lib.mertens_table_info.argtypes = [P, ctypes.POINTER(u64), ctypes.POINTER(mertens_u128),
+                                           ctypes.POINTER(sz)]
+        lib.mertens_table_info.restype = c_int
+        lib.mertens_plan_on_table.argtypes = [ctypes.POINTER(P), P, ctypes.POINTER(mertens_u128),
+                                              sz, mertens_u128, u64]
+        lib.mertens_plan_on_table.restype = c_int
+        lib.mertens_server_use_table.argtypes = [P, P]
+        lib.mertens_server_use_table.restype = c_int
+        lib.mertens_table_destroy.argtypes = [P]
+        lib.mertens_table_destroy.restype = None
         lib.mertens_run.argtypes = [P, P]
         lib.mertens_run.restype = c_int
         lib.mertens_result.argtypes = [P, sz, ctypes.POINTER(i64), P, sz,
@@ -237,6 +251,44 @@ def mertens_window_result(plan: int, i: int = 0):
     _check(lib.mertens_window_result(plan, i, S.ctypes.data, c.ctypes.data, X, ctypes.byref(ln),
                                      ctypes.byref(mu)), "mertens_window_result")
     return S, c, int(mu.value)
+
+
+def mertens_table_create(y_max: int, n_max: int, stream=None) -> int:
+    """Sieves M(y), y <= y_max, into a resident device table (with the
+    update's target-independent parts for n <= n_max); returns its handle."""
+    h = ctypes.c_void_p()
+    _check(load().mertens_table_create(ctypes.byref(h), int(y_max), u128(n_max),
+                                       _stream(stream)), "mertens_table_create")
+    return int(h.value)
+
+
+def mertens_table_info(table: int) -> dict:
+    y = ctypes.c_uint64()
+    nm = mertens_u128()
+    b = ctypes.c_size_t()
+    _check(load().mertens_table_info(table, ctypes.byref(y), ctypes.byref(nm), ctypes.byref(b)),
+           "mertens_table_info")
+    return dict(y_max=y.value, n_max=nm.lo | (nm.hi << 64), bytes=b.value)
+
+
+def mertens_plan_on_table(table: int, n, u: int = 0, block_len: int = 0) -> int:
+    """A plan whose M(y) comes from the resident table (no sieve)."""
+    lib = load()
+    ns = [int(n)] if isinstance(n, (int, np.integer)) else [int(v) for v in n]
+    arr = (mertens_u128 * len(ns))(*[u128(v) for v in ns])
+    h = ctypes.c_void_p()
+    _check(lib.mertens_plan_on_table(ctypes.byref(h), table, arr, len(ns), u128(u),
+                                     int(block_len)), "mertens_plan_on_table")
+    return int(h.value)
+
+
+def mertens_server_use_table(srv: int, table: int) -> None:
+    _check(load().mertens_server_use_table(srv, table), "mertens_server_use_table")
+
+
+def mertens_table_destroy(table: int) -> None:
+    if table:
+        load().mertens_table_destroy(table)
 
 
 def mertens_run(plan: int, stream=None) -> None:

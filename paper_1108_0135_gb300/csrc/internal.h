@@ -3,6 +3,8 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <utility>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "../../include/libmertens.h"
@@ -84,5 +86,33 @@ int exclusive_scan_u32(const uint32_t *in, uint32_t *out, size_t n, uint32_t *sc
 
 // Thread-local last-error text.
 void set_last_error(const char *fmt, ...);
+
+// Device bytes of the Granlund-Montgomery magic table and of the dense
+// squarefree list (update.cu) for a dense limit ydense.
+inline uint64_t dense_chunks(uint64_t ydense) { return ydense / kChunk + 1; }
+
+}  // namespace mert
+
+// A resident M(y) table (mertens_table_create): M(y) for 1 <= y <= y_max in
+// the sieve's block layout (int16 relative to the 2048-y segment, int64
+// segment offsets, both indexed from y = 1), and the query-independent parts
+// of the update for targets up to n_max: divisor magics for d < mg_n and the
+// squarefree dense list for y <= ydense.
+struct mertens_table_s {
+    mert::Allocator al;
+    int device = 0;
+    uint64_t y_max = 0;
+    uint64_t n_max_lo = 0, n_max_hi = 0;
+    uint64_t ydense = 0, mg_n = 0;
+    int16_t *Mloc = nullptr;
+    int64_t *segoff = nullptr;
+    uint64_t *MG = nullptr, *dl_m = nullptr;
+    uint16_t *dl_yo = nullptr;
+    uint32_t *dl_cnt = nullptr;
+    size_t bytes = 0;
+    std::vector<std::pair<void *, size_t>> allocs;
+};
+
+namespace mert {
 
 }  // namespace mert

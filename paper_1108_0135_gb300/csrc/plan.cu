@@ -177,6 +177,12 @@ struct mertens_plan_s {
     uint64_t y_first = 1, y_last = 0;
     bool window = false;
     std::vector<uint64_t> coef;
+    // plans on a resident table: M(y), the divisor magics and the dense list
+    // are the table's; targets n <= table y_max are read from it directly
+    // (entry, y) pairs
+    mertens_table_s *table = nullptr;
+    std::vector<uint64_t> lookups;
+    uint64_t *dlook = nullptr;
     mertens_tuning tuning{};
     uint64_t terms = 0, dense_y = 0, gather_j = 0;
     double sieve_updates = 0;
@@ -286,19 +292,13 @@ static int describe_target(u128 n, uint64_t u, uint64_t *X, uint64_t *direct,
     return 0;
 }
 
-// u = f (count n)^(2/3) count^(-1/5): the sieve costs ~u and the update
-// ~count sqrt(n n/u), balanced at u ~ (count n)^(2/3) (Sec. 2); the extra
-// count^(-1/5) and f = 0.45 are what the autotuner measured on GB300 for
-// single targets (0.45) and batches of 8 (0.3).
-static uint64_t auto_u(u128 n, size_t count, const mertens_tuning &t)
+// Sieve limit of one target given the batch's shared limit ub: as large as
+// ub but above floor(sqrt(n)) and at most n.
+static uint64_t target_u(u128 n, double ub)
 {
     if (n <= 3)
         return (uint64_t)n;
-    const char *e = getenv("MERTENS_U_FACTOR");
-    const double f = e ? atof(e) : (t.u_factor > 0 ? t.u_factor : 0.45);
-    const double ud = f * std::pow((double)n * (double)count, 2.0 / 3.0) *
-                      std::pow((double)count, -0.2);
-    uint64_t u = ud >= 1.8e19 ? UINT64_MAX : (uint64_t)ud;
+    uint64_t u = ub >= 1.8e19 ? UINT64_MAX : (uint64_t)ub;
     const uint64_t r = isqrt128(n);
     if (u <= r)
         u = r + 1;
@@ -307,9 +307,46 @@ static uint64_t auto_u(u128 n, size_t count, const mertens_tuning &t)
     return u;
 }
 
+// Shared sieve limit of a batch: ub = f (sum n)^(2/3) Neff^(-1/5) with
+// Neff = sum n / max n.  The sieve costs ~ub and the update ~sum_i n_i/sqrt(u_i)
+// (Sec. 2), balanced at ub ~ (sum n)^(2/3); every target then takes
+// u_i = min(n_i, ub) (a small target costs no extra sieve and fewer terms
+// the larger its u).  For count equal targets this is f (count n)^(2/3)
+// count^(-1/5); the count^(-1/5) and f = 0.45 are what the autotuner measured
+// on GB300 for single targets (0.45) and batches of 8 (0.3).
+static double batch_ub(const std::vector<u128> &ns, const mertens_tuning &t)
+{
+    const char *e = getenv("MERTENS_U_FACTOR");
+    const double f = e ? atof(e) : (t.u_factor > 0 ? t.u_factor : 0.45);
+    double sum = 0, mx = 0;
+    for (u128 n : ns) {
+        sum += (double)n;
+        mx = std::max(mx, (double)n);
+    }
+    if (mx <= 0)
+        return 1;
+    return f * std::pow(sum, 2.0 / 3.0) * std::pow(sum / mx, -0.2);
+}
+
+static uint64_t auto_u(u128 n, size_t count, const mertens_tuning &t)
+{
+    std::vector<u128> ns(count ? count : 1, n);
+    return target_u(n, batch_ub(ns, t));
+}
+
 namespace mert {
-// The sieve limit the library picks for target n in a batch of `count`.
-uint64_t plan_auto_u(uint64_t n, size_t count) { return auto_u(n, count, tuning_now()); }
+// Dense cut-off factor of new plans (c in y_c ~ c sqrt(k)).
+double plan_dense_factor() { return dense_factor(tuning_now()); }
+// The sieve limits the library picks for the targets of a batch.
+std::vector<uint64_t> plan_auto_u(const std::vector<uint64_t> &ns)
+{
+    std::vector<u128> v(ns.begin(), ns.end());
+    const double ub = batch_ub(v, tuning_now());
+    std::vector<uint64_t> out;
+    for (uint64_t n : ns)
+        out.push_back(target_u(n, ub));
+    return out;
+}
 // Device bytes a plan holds (its buffers and its prime table).
 size_t plan_device_bytes(mertens_plan_t p)
 {
@@ -322,6 +359,14 @@ size_t plan_device_bytes(mertens_plan_t p)
     return b;
 }
 }  // namespace mert
+
+// Sieve limit of a target on a resident table of M(y), y <= y_max: as large
+// as the table allows (the update's terms fall as 1/sqrt(u)).
+static uint64_t table_u(u128 n, uint64_t y_max)
+{
+    const u128 u = (u128)y_max + 1;
+    return (uint64_t)(n < u ? n : u);
+}
 
 static int check_u(u128 n, uint64_t u)
 {
@@ -420,7 +465,8 @@ int mertens_describe(mertens_u128 n, mertens_u128 u, mertens_query_info *info)
 
 static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count, mertens_u128 u,
                        uint64_t block_len, const mertens_tuning &tn, bool window = false,
-                       uint64_t w_first = 1, uint64_t w_last = UINT64_MAX)
+                       uint64_t w_first = 1, uint64_t w_last = UINT64_MAX,
+                       mertens_table_s *table = nullptr)
 {
     if (!out)
         return MERTENS_EINVAL;
@@ -433,9 +479,14 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
         set_last_error("mertens_plan: u >= 2^64 is not supported by this build");
         return MERTENS_ENOTSUP;
     }
-    for (size_t i = 0; i < count; ++i) {
+    for (size_t i = 0; i < count; ++i)
         if (check_n(n[i], "mertens_plan", i) != MERTENS_OK)
             return MERTENS_EINVAL;
+    std::vector<u128> n128(count);
+    for (size_t i = 0; i < count; ++i)
+        n128[i] = to_u128(n[i]);
+    const double ub = batch_ub(n128, tn);
+    for (size_t i = 0; i < count; ++i) {
         const u128 nn = to_u128(n[i]);
         if (u.lo != 0 && check_u(nn, u.lo) != MERTENS_OK) {
             set_last_error("mertens_plan: u = %llu invalid for n[%zu] "
@@ -443,7 +494,17 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
                            (unsigned long long)u.lo, i);
             return MERTENS_EINVAL;
         }
-        const uint64_t uu = u.lo ? u.lo : auto_u(nn, count, tn);
+        if (table) {
+            const u128 nmax = ((u128)table->n_max_hi << 64) | table->n_max_lo;
+            const uint64_t ut = u.lo ? u.lo : table_u(nn, table->y_max);
+            if (nn > nmax || (nn > table->y_max && (ut > table->y_max + 1 ||
+                                                     check_u(nn, ut) != MERTENS_OK))) {
+                set_last_error("mertens_plan_on_table: n[%zu] is beyond the table (n_max, or "
+                               "u <= y_max + 1 with u > sqrt(n))", i);
+                return MERTENS_ENOTSUP;
+            }
+        }
+        const uint64_t uu = u.lo ? u.lo : (table ? table_u(nn, table->y_max) : target_u(nn, ub));
         if (nn / uu >= ((u128)1 << 32)) {
             set_last_error("mertens_plan: n[%zu]/u >= 2^32 array entries", i);
             return MERTENS_ENOTSUP;
@@ -462,7 +523,7 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
     std::vector<Group> groups;
     for (size_t i = 0; i < count; ++i) {
         const u128 nn = to_u128(n[i]);
-        const uint64_t uu = u.lo ? u.lo : auto_u(nn, count, tn);
+        const uint64_t uu = u.lo ? u.lo : (table ? table_u(nn, table->y_max) : target_u(nn, ub));
         const uint64_t X = (uint64_t)(nn / uu);
         p->n.push_back((uint64_t)nn);
         p->n_hi.push_back((uint64_t)(nn >> 64));
@@ -470,6 +531,26 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
         p->X.push_back(X);
         p->off.push_back(K.size());
         uint64_t d = 0, g = 0, ymq = 0;
+        if (table && nn <= table->y_max && X == 1) {
+            // M(n) is in the table: one entry, no terms, read after resolve
+            p->lookups.push_back(K.size());
+            p->lookups.push_back((uint64_t)nn);
+            K.push_back(0);
+            JLO.push_back(1);
+            YCE.push_back(0);
+            JC0.push_back(0);
+            Group G;
+            G.first = (uint32_t)(K.size() - 1);
+            G.count = 1;
+            G.pred = 1;
+            G.pad = 0;
+            G.yc = 0;
+            groups.push_back(G);
+            p->direct.push_back(0);
+            p->gathered.push_back(0);
+            p->ymax_q.push_back(0);
+            continue;
+        }
         std::vector<uint64_t> S_(32), VH(32);
         std::vector<uint8_t> WD(32);
         const u128 wide_from = wide_threshold();
@@ -588,6 +669,16 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
         delete p;
         return MERTENS_ENOTSUP;
     }
+    p->table = table;
+    if (table) {
+        if (block_len == 0)
+            block_len = 1ull << 30;
+        if (block_len % kSegY) {
+            set_last_error("mertens_plan_on_table: block_len must be a multiple of %d", kSegY);
+            delete p;
+            return MERTENS_EINVAL;
+        }
+    }
     p->window = window;
     p->y_first = window ? w_first : 1;
     p->y_last = window ? std::min(w_last, p->y_max) : p->y_max;
@@ -617,6 +708,13 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
                 p->jmax = std::max(p->jmax, std::min(JC0[e], K[e] / p->y_first));
     }
     p->mg_n = std::max(p->jmax, p->ydense) + 1;
+    if (table && (p->y_max > table->y_max || p->ydense > table->ydense ||
+                  p->mg_n > table->mg_n)) {
+        set_last_error("mertens_plan_on_table: the targets need y, dense cut-offs or divisors "
+                       "beyond the table");
+        delete p;
+        return MERTENS_ENOTSUP;
+    }
 
     // ---- dense work items: groups sorted by cut-off, chunk ranges ----
     std::vector<uint32_t> order(groups.size());
@@ -820,22 +918,38 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
     p->dScan = p->alloc<uint32_t>(scan_scratch_words(E));
     const uint64_t L = block_len;
     const uint64_t nseg = sieve_segments(L);
-    p->dmu_aux = p->alloc<int8_t>(p->ydense + 16);
     // One stream by default: on GB300 the three-stream schedule measured
     // slower (the sieve and the updates contend for the same SM resources);
-    // MERTENS_OVERLAP=1 selects it.
-    p->serial = getenv("MERTENS_OVERLAP") == nullptr || p->nblocks == 1;
-    const int nbuf = p->serial ? 1 : 2;
-    for (int i = 0; i < 2; ++i) {
-        if (i < nbuf) {
-            p->dMloc[i] = p->alloc<int16_t>(L + 2);
-            p->dsegsum[i] = p->alloc<int32_t>(nseg);
-            p->dsegoff[i] = p->alloc<int64_t>(nseg);
-        } else {
-            p->dMloc[i] = p->dMloc[0];
-            p->dsegsum[i] = p->dsegsum[0];
-            p->dsegoff[i] = p->dsegoff[0];
+    // MERTENS_OVERLAP=1 selects it.  Plans on a table have no sieve.
+    p->serial = getenv("MERTENS_OVERLAP") == nullptr || p->nblocks == 1 || table;
+    if (table) {
+        // the table's M(y) blocks are addressed per block at run time
+        p->dmu_aux = nullptr;
+        p->dMG = table->MG;
+        p->ddl_m = table->dl_m;
+        p->ddl_yo = table->dl_yo;
+        p->ddl_cnt = table->dl_cnt;
+        p->mg_built = true;
+        if (!p->lookups.empty())
+            p->dlook = p->alloc<uint64_t>(p->lookups.size());
+    } else {
+        p->dmu_aux = p->alloc<int8_t>(p->ydense + 16);
+        const int nbuf = p->serial ? 1 : 2;
+        for (int i = 0; i < 2; ++i) {
+            if (i < nbuf) {
+                p->dMloc[i] = p->alloc<int16_t>(L + 2);
+                p->dsegsum[i] = p->alloc<int32_t>(nseg);
+                p->dsegoff[i] = p->alloc<int64_t>(nseg);
+            } else {
+                p->dMloc[i] = p->dMloc[0];
+                p->dsegsum[i] = p->dsegsum[0];
+                p->dsegoff[i] = p->dsegoff[0];
+            }
         }
+        p->dMG = p->alloc<uint64_t>(p->mg_n + 1);
+        p->ddl_m = p->alloc<uint64_t>(nchunks * kChunkCapPad);
+        p->ddl_yo = p->alloc<uint16_t>(nchunks * kChunkCapPad);
+        p->ddl_cnt = p->alloc<uint32_t>(nchunks);
     }
     p->dcarry = p->alloc<int64_t>(p->nblocks + 1);
     p->dgtiles = p->alloc<GatherTile>(gtiles.size() + 1);
@@ -845,10 +959,6 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
     p->dcounter = p->alloc<uint32_t>(1);
     p->dcounter_dense = p->alloc<uint32_t>(1);
     p->dcounter_gather = p->alloc<uint32_t>(1);
-    p->dMG = p->alloc<uint64_t>(p->mg_n + 1);
-    p->ddl_m = p->alloc<uint64_t>(nchunks * kChunkCapPad);
-    p->ddl_yo = p->alloc<uint16_t>(nchunks * kChunkCapPad);
-    p->ddl_cnt = p->alloc<uint32_t>(nchunks);
     p->dgroups = p->alloc<Group>(sg.size());
     p->ditems = p->alloc<DenseItem>(items.size());
     p->dqs = p->alloc<QueryDev>(count);
@@ -859,20 +969,22 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
             rc = MERTENS_ENOMEM;
     bool any_null = !p->dK || !p->dJLO || !p->dJC0 || !p->dJCUR || !p->dYCE || !p->dJTOP ||
                     !p->dJBOT || !p->dS || !p->dR || !p->dICNT || !p->dIOFF || !p->dScan ||
-                    !p->dmu_aux || !p->dMloc[0] || !p->dsegsum[0] || !p->dsegoff[0] ||
-                    !p->dMloc[1] || !p->dsegsum[1] || !p->dsegoff[1] || !p->dgtiles ||
+                    (!table && (!p->dmu_aux || !p->dMloc[0] || !p->dsegsum[0] ||
+                                !p->dsegoff[0] || !p->dMloc[1] || !p->dsegsum[1] ||
+                                !p->dsegoff[1])) ||
+                    (!p->lookups.empty() && !p->dlook) || !p->dgtiles ||
                     !p->dcounter_dense || !p->dcounter_gather ||
                     !p->dgitems || !p->dcarry || !p->derr || !p->dcounter || !p->dMG ||
                     !p->ddl_m || !p->ddl_yo || !p->ddl_cnt || !p->dgroups || !p->ditems ||
                     !p->dqs || (!p->wide.empty() && !p->dwide);
     if (any_null)
         rc = MERTENS_ENOMEM;
-    if (rc == MERTENS_OK) {
+    if (rc == MERTENS_OK && !table) {
         int prc = prime_table_create(&p->pt, p->al, std::max<uint64_t>(p->y_last, 1), nullptr);
         if (prc != 0)
             rc = prc == 6 ? MERTENS_ENOTSUP : (prc == 2 ? MERTENS_ENOMEM : MERTENS_ECUDA);
     }
-    if (rc == MERTENS_OK) {
+    if (rc == MERTENS_OK && !table) {
         // algorithmic sieve updates: each block of length len sieved with the
         // primes p <= max(7, sqrt(block end)) costs len * sum (1/p + 1/p^2)
         std::vector<double> pre(p->pt.np + 1, 0.0);
@@ -904,6 +1016,9 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
         cudaMemcpy(p->dqs, qs.data(), count * sizeof(QueryDev), cudaMemcpyHostToDevice);
         if (!p->wide.empty())
             cudaMemcpy(p->dwide, p->wide.data(), p->wide.size() * sizeof(WideEntry),
+                       cudaMemcpyHostToDevice);
+        if (!p->lookups.empty())
+            cudaMemcpy(p->dlook, p->lookups.data(), p->lookups.size() * 8,
                        cudaMemcpyHostToDevice);
         if (!gtiles.empty())
             cudaMemcpy(p->dgtiles, gtiles.data(), gtiles.size() * sizeof(GatherTile),
@@ -1043,9 +1158,10 @@ static int run_enqueue(mertens_plan_s *p, cudaStream_t origin, uint64_t *out)
     }
     cudaMemsetAsync(p->dS, 0, E * 8, su);
     cudaMemcpyAsync(p->dJCUR, p->dJC0, E * 8, cudaMemcpyDeviceToDevice, su);
+    const mertens_table_s *tab = p->table;
     cudaMemsetAsync(p->dcarry, 0, 8 * (p->nblocks + 1), ss);
     cudaMemsetAsync(p->derr, 0, 4, su);
-    if (p->window && p->y_first <= p->ydense)
+    if (p->window && p->y_first <= p->ydense && !tab)
         cudaMemsetAsync(p->dmu_aux, 0, p->ydense + 1, ss);  // mu outside the window: none
     if (!p->mg_built) {
         r = magic_table_enqueue(p->dMG, p->mg_n, su);
@@ -1064,73 +1180,102 @@ static int run_enqueue(mertens_plan_s *p, cudaStream_t origin, uint64_t *out)
         // window's end); a window above Y_dense has none
         bool dense_done = p->y_first > p->ydense;
         const uint64_t dense_at = std::min(p->ydense, p->y_last);
+        if (tab && !dense_done) {
+            // the squarefree list is the table's: the dense part needs no block
+            PhaseEvents pe;
+            ev_begin(p, kPhDense, su, &pe);
+            DenseArgs da;
+            da.items = p->ditems;
+            da.nitems = p->nitems;
+            da.counter = p->dcounter_dense;
+            da.groups = p->dgroups;
+            da.K = p->dK;
+            da.YCE = p->dYCE;
+            da.dl_m = p->ddl_m;
+            da.dl_yo = p->ddl_yo;
+            da.dl_cnt = p->ddl_cnt;
+            da.S = p->dS;
+            da.ctas_per_sm = 0;
+            r = dense_update_enqueue(da, su);
+            ev_end(p, su, &pe);
+            if (r < 0)
+                goto fail;
+            launches += r;
+            dense_done = true;
+        }
         for (uint64_t b = 0; b < p->nblocks; ++b) {
             uint64_t y1, y2;
             block_range(p, b, &y1, &y2);
             const int buf = (int)(b & 1);
+            // M(y) of the block: the plan's buffer (sieved below) or the table's
+            const int16_t *Mb = tab ? tab->Mloc + (y1 - 1) : p->dMloc[buf];
+            const int64_t *Sb = tab ? tab->segoff + ((y1 - 1) >> kSegShift) : p->dsegoff[buf];
             if (!serial && b >= 2)
                 cudaStreamWaitEvent(ss, p->ev_upd[b - 2], 0);
             cudaStream_t s = ss;
-            SieveLaunch L;
-            L.y1 = y1;
-            L.len = y2 - y1 + 1;
-            L.Mloc = p->dMloc[buf];
-            L.segsum = p->dsegsum[buf];
-            L.segoff = p->dsegoff[buf];
-            L.carry_in = p->dcarry + b;
-            L.carry_out = p->dcarry + b + 1;
-            L.mu_out = (y1 <= p->ydense) ? p->dmu_aux : nullptr;
-            L.mu_base = 1;
-            L.mu_end = p->ydense;
-            PhaseEvents pe, pe2;
-            ev_begin(p, kPhSieve, s, &pe);
-            if (p->prof) {
-                pe2.phase = kPhScan;
-                cudaEventCreate(&pe2.a);
-                cudaEventCreate(&pe2.b);
-                L.mid = pe.b;
-                L.mid2 = pe2.a;
-            }
-            r = sieve_block_enqueue(&p->pt, L, s);
-            if (p->prof) {
-                p->evs.push_back(pe);
-                cudaEventRecord(pe2.b, s);
-                p->evs.push_back(pe2);
-            }
-            if (r < 0)
-                goto fail;
-            launches += r;
-            if (!serial)
-                cudaEventRecord(p->ev_sieved[b], ss);
-            if (!dense_done && y2 >= dense_at) {
-                s = sd;
+            if (!tab) {
+                SieveLaunch L;
+                L.y1 = y1;
+                L.len = y2 - y1 + 1;
+                L.Mloc = p->dMloc[buf];
+                L.segsum = p->dsegsum[buf];
+                L.segoff = p->dsegoff[buf];
+                L.carry_in = p->dcarry + b;
+                L.carry_out = p->dcarry + b + 1;
+                L.mu_out = (y1 <= p->ydense) ? p->dmu_aux : nullptr;
+                L.mu_base = 1;
+                L.mu_end = p->ydense;
+                PhaseEvents pe, pe2;
+                ev_begin(p, kPhSieve, s, &pe);
+                if (p->prof) {
+                    pe2.phase = kPhScan;
+                    cudaEventCreate(&pe2.a);
+                    cudaEventCreate(&pe2.b);
+                    L.mid = pe.b;
+                    L.mid2 = pe2.a;
+                }
+                r = sieve_block_enqueue(&p->pt, L, s);
+                if (p->prof) {
+                    p->evs.push_back(pe);
+                    cudaEventRecord(pe2.b, s);
+                    p->evs.push_back(pe2);
+                }
+                if (r < 0)
+                    goto fail;
+                launches += r;
                 if (!serial)
-                    cudaStreamWaitEvent(sd, p->ev_sieved[b], 0);
-                ev_begin(p, kPhDense, s, &pe);
-                r = dense_list_enqueue(p->dmu_aux, p->ydense, p->dMG, p->ddl_m, p->ddl_yo,
-                                       p->ddl_cnt, s);
-                if (r < 0)
-                    goto fail;
-                launches += r;
-                DenseArgs da;
-                da.items = p->ditems;
-                da.nitems = p->nitems;
-                da.counter = p->dcounter_dense;
-                da.groups = p->dgroups;
-                da.K = p->dK;
-                da.YCE = p->dYCE;
-                da.dl_m = p->ddl_m;
-                da.dl_yo = p->ddl_yo;
-                da.dl_cnt = p->ddl_cnt;
-                da.S = p->dS;
-                da.ctas_per_sm = serial ? 0 : 1;
-                r = dense_update_enqueue(da, s);
-                ev_end(p, s, &pe);
-                if (r < 0)
-                    goto fail;
-                launches += r;
-                dense_done = true;
-            }
+                    cudaEventRecord(p->ev_sieved[b], ss);
+                if (!dense_done && y2 >= dense_at) {
+                    s = sd;
+                    if (!serial)
+                        cudaStreamWaitEvent(sd, p->ev_sieved[b], 0);
+                    ev_begin(p, kPhDense, s, &pe);
+                    r = dense_list_enqueue(p->dmu_aux, p->ydense, p->dMG, p->ddl_m, p->ddl_yo,
+                                           p->ddl_cnt, s);
+                    if (r < 0)
+                        goto fail;
+                    launches += r;
+                    DenseArgs da;
+                    da.items = p->ditems;
+                    da.nitems = p->nitems;
+                    da.counter = p->dcounter_dense;
+                    da.groups = p->dgroups;
+                    da.K = p->dK;
+                    da.YCE = p->dYCE;
+                    da.dl_m = p->ddl_m;
+                    da.dl_yo = p->ddl_yo;
+                    da.dl_cnt = p->ddl_cnt;
+                    da.S = p->dS;
+                    da.ctas_per_sm = serial ? 0 : 1;
+                    r = dense_update_enqueue(da, s);
+                    ev_end(p, s, &pe);
+                    if (r < 0)
+                        goto fail;
+                    launches += r;
+                    dense_done = true;
+                }
+            }  // sieve of the block
+            PhaseEvents pe;
             s = su;
             if (!serial)
                 cudaStreamWaitEvent(su, p->ev_sieved[b], 0);
@@ -1154,8 +1299,8 @@ static int run_enqueue(mertens_plan_s *p, cudaStream_t origin, uint64_t *out)
             sa.S = p->dS;
             sa.ICNT = p->dICNT;
             sa.IOFF = p->dIOFF;
-            sa.Mloc = p->dMloc[buf];
-            sa.segoff = p->dsegoff[buf];
+            sa.Mloc = Mb;
+            sa.segoff = Sb;
             sa.y_lo = p->gend[b] + 1 > y1 ? p->gend[b] + 1 : y1;
             sa.m_ylo = magic_of(sa.y_lo);
             sa.l_ylo = magic_shift(sa.y_lo);
@@ -1166,8 +1311,8 @@ static int run_enqueue(mertens_plan_s *p, cudaStream_t origin, uint64_t *out)
                 ga.items = p->dgitems + p->gblk[b];
                 ga.nitems = p->gblk[b + 1] - p->gblk[b];
                 ga.counter = p->dcounter_gather;
-                ga.Mloc = p->dMloc[buf];
-                ga.segoff = p->dsegoff[buf];
+                ga.Mloc = Mb;
+                ga.segoff = Sb;
                 ga.threads = serial ? 512 : 256;
                 ga.ctas_per_sm = serial ? 0 : 2;
                 ga.K = p->dK;
@@ -1193,8 +1338,8 @@ static int run_enqueue(mertens_plan_s *p, cudaStream_t origin, uint64_t *out)
                 wa.W = p->dwide;
                 wa.y1 = y1;
                 wa.y2 = y2;
-                wa.Mloc = p->dMloc[buf];
-                wa.segoff = p->dsegoff[buf];
+                wa.Mloc = Mb;
+                wa.segoff = Sb;
                 wa.S = p->dS;
                 ev_begin(p, kPhGather, s, &pe);
                 r = wide_update_enqueue(wa, (uint32_t)p->wide.size(), p->wide_grid[b], s);
@@ -1217,6 +1362,11 @@ static int run_enqueue(mertens_plan_s *p, cudaStream_t origin, uint64_t *out)
             PhaseEvents pe;
             ev_begin(p, kPhResolve, su, &pe);
             r = resolve_enqueue(p->dqs, (uint32_t)p->nq, p->dS, p->dK, p->dR, su);
+            if (r >= 0 && !p->lookups.empty()) {
+                const int r2 = table_lookup_enqueue(p->dlook, (uint32_t)(p->lookups.size() / 2),
+                                                    tab->Mloc, tab->segoff, p->dR, su);
+                r = r2 < 0 ? r2 : r + r2;
+            }
             ev_end(p, su, &pe);
             if (r < 0)
                 goto fail;
@@ -1245,7 +1395,7 @@ int mertens_run(mertens_plan_t p, void *stream)
     }
     cudaStream_t s = (cudaStream_t)stream;
     uint64_t launches = 0;
-    const bool graph_ok = !p->prof && p->mg_built && !getenv("MERTENS_NO_GRAPH");
+    const bool graph_ok = !p->prof && p->ran && !getenv("MERTENS_NO_GRAPH");
     if (!graph_ok) {
         PhaseEvents total;
         ev_begin(p, kPhTotal, s, &total);
@@ -1346,6 +1496,25 @@ int mertens_result(mertens_plan_t p, size_t i, int64_t *M_n, int64_t *entries, s
         p->d2h_bytes += m * 8;
     }
     return MERTENS_OK;
+}
+
+int mertens_plan_on_table(mertens_plan_t *out, mertens_table_t table, const mertens_u128 *n,
+                          size_t count, mertens_u128 u, uint64_t block_len)
+{
+    if (out)
+        *out = nullptr;
+    if (!table) {
+        set_last_error("mertens_plan_on_table: NULL table");
+        return MERTENS_EINVAL;
+    }
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != table->device) {
+        set_last_error("mertens_plan_on_table: the table lives on device %d, current is %d",
+                       table->device, dev);
+        return MERTENS_EINVAL;
+    }
+    return plan_create(out, n, count, u, block_len, tuning_now(), false, 1, UINT64_MAX, table);
 }
 
 int mertens_plan_window(mertens_plan_t *out, const mertens_u128 *n, size_t count,

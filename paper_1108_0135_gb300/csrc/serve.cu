@@ -22,7 +22,7 @@
 #include "internal.h"
 
 namespace mert {
-uint64_t plan_auto_u(uint64_t n, size_t count);
+std::vector<uint64_t> plan_auto_u(const std::vector<uint64_t> &ns);
 size_t plan_device_bytes(mertens_plan_t p);
 }  // namespace mert
 
@@ -56,14 +56,24 @@ struct Inflight {
     size_t bytes = 0;
 };
 
+// Device memory of a batch planned on a resident table: entry arrays only.
+size_t estimate_table_batch_bytes(const std::vector<uint64_t> &ns, uint64_t y_max)
+{
+    double entries = 0;
+    for (uint64_t n : ns)
+        entries += (double)(n / std::min<uint64_t>(n, y_max + 1));
+    return (size_t)(110.0 * entries + 64.0e6);
+}
+
 // Device memory a batch's plan will take, estimated from the plan's shapes
 // (entry arrays, one sieve block of int16 M, the divisor-magic table and the
 // squarefree list up to the dense cut-off ~1.6 sqrt(n)), with slack.
 size_t estimate_batch_bytes(const std::vector<uint64_t> &ns)
 {
     double entries = 0, ymax = 0, nmax = 0;
-    for (uint64_t n : ns) {
-        const uint64_t u = plan_auto_u(n, ns.size());
+    const std::vector<uint64_t> us = plan_auto_u(ns);
+    for (size_t i = 0; i < ns.size(); ++i) {
+        const uint64_t n = ns[i], u = us[i];
         entries += (double)(n / u);
         ymax = std::max(ymax, (double)u);
         nmax = std::max(nmax, (double)n);
@@ -78,7 +88,7 @@ size_t estimate_batch_bytes(const std::vector<uint64_t> &ns)
 struct mertens_server_s {
     int device = 0;
     size_t budget = 0;
-    uint32_t max_inflight = 4, max_batch = 64;
+    uint32_t max_inflight = 4, max_batch = 128;
     std::mutex mu;
     std::condition_variable cv;
     std::deque<Query> queue;
@@ -88,6 +98,7 @@ struct mertens_server_s {
     std::thread worker;
     std::vector<cudaStream_t> streams;
     mertens_server_stats st{};
+    mertens_table_t table = nullptr;  // when set, batches that fit are planned on it
     int init_status = MERTENS_OK;
     bool ready = false;
 
@@ -173,10 +184,13 @@ struct mertens_server_s {
                     std::lock_guard<std::mutex> lk(mu);
                     if (queue.empty())
                         break;
-                    // classes of a factor 4 in n: one sieve limit suits all
-                    const unsigned cls = bitlen64(queue.front().n) / 2;
+                    // classes of a factor 2^20 in n: a batch shares one sieve
+                    // limit set by its largest targets (smaller ones take
+                    // u = min(n, that limit)), and small queries do not wait
+                    // behind the largest ones
+                    const unsigned cls = bitlen64(queue.front().n) / 20;
                     for (auto it = queue.begin(); it != queue.end() && batch.size() < max_batch;) {
-                        if (bitlen64(it->n) / 2 == cls) {
+                        if (bitlen64(it->n) / 20 == cls) {
                             batch.push_back(*it);
                             it = queue.erase(it);
                         } else {
@@ -187,7 +201,18 @@ struct mertens_server_s {
                 std::vector<uint64_t> ns;
                 for (const Query &q : batch)
                     ns.push_back(q.n);
-                const size_t est = estimate_batch_bytes(ns);
+                mertens_table_t tab = nullptr;
+                {
+                    std::lock_guard<std::mutex> lk(mu);
+                    tab = table;
+                }
+                uint64_t nmax = 0;
+                for (uint64_t v : ns)
+                    nmax = std::max(nmax, v);
+                if (tab && (tab->n_max_hi == 0 && nmax > tab->n_max_lo))
+                    tab = nullptr;
+                const size_t est = tab ? estimate_table_batch_bytes(ns, tab->y_max)
+                                       : estimate_batch_bytes(ns);
                 auto put_back = [&]() {
                     std::lock_guard<std::mutex> lk(mu);
                     for (auto it = batch.rbegin(); it != batch.rend(); ++it)
@@ -204,7 +229,11 @@ struct mertens_server_s {
                 }
                 mertens_u128 u0 = {0, 0};
                 Inflight f;
-                int rc = mertens_plan(&f.plan, nv.data(), nv.size(), u0, 0);
+                int rc = MERTENS_ENOTSUP;
+                if (tab)
+                    rc = mertens_plan_on_table(&f.plan, tab, nv.data(), nv.size(), u0, 0);
+                if (rc == MERTENS_ENOTSUP)
+                    rc = mertens_plan(&f.plan, nv.data(), nv.size(), u0, 0);
                 if (rc == MERTENS_ENOMEM && !inflight.empty()) {
                     put_back();
                     break;
@@ -259,7 +288,7 @@ int mertens_server_create(mertens_server_t *out, int device, size_t mem_budget_b
     if (max_inflight == 0)
         max_inflight = 4;
     if (max_batch == 0)
-        max_batch = 64;
+        max_batch = 128;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
         cudaGetLastError();
@@ -291,6 +320,21 @@ int mertens_server_create(mertens_server_t *out, int device, size_t mem_budget_b
         return rc;
     }
     *out = s;
+    return MERTENS_OK;
+}
+
+int mertens_server_use_table(mertens_server_t s, mertens_table_t table)
+{
+    if (!s) {
+        set_last_error("mertens_server_use_table: NULL server");
+        return MERTENS_EINVAL;
+    }
+    if (table && table->device != s->device) {
+        set_last_error("mertens_server_use_table: the table lives on another device");
+        return MERTENS_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->table = table;
     return MERTENS_OK;
 }
 

@@ -598,6 +598,26 @@ __global__ void __launch_bounds__(kWideThreads) wide_update_kernel(WideArgs a)
     }
 }
 
+__global__ void table_lookup_kernel(const uint64_t *__restrict__ pairs, uint32_t count,
+                                    const int16_t *__restrict__ Mloc,
+                                    const int64_t *__restrict__ segoff, uint64_t *__restrict__ R)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count)
+        return;
+    const uint64_t y = pairs[2 * i + 1];
+    R[pairs[2 * i]] = (uint64_t)(segoff[(y - 1) >> kSegShift] + (int64_t)Mloc[y - 1]);
+}
+
+int table_lookup_enqueue(const uint64_t *pairs, uint32_t count, const int16_t *Mloc,
+                         const int64_t *segoff, uint64_t *R, cudaStream_t s)
+{
+    if (count == 0)
+        return 0;
+    table_lookup_kernel<<<(count + 255) / 256, 256, 0, s>>>(pairs, count, Mloc, segoff, R);
+    return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
 int wide_update_enqueue(const WideArgs &a, uint32_t nw, uint32_t grid_x, cudaStream_t s)
 {
     if (nw == 0 || grid_x == 0)

@@ -15,12 +15,16 @@ import numpy as np
 from . import _lib as L
 
 
-def run_stream(ns, arrivals_s=None, device=0, max_inflight=0, max_batch=0, mem_budget=0):
+def run_stream(ns, arrivals_s=None, device=0, max_inflight=0, max_batch=0, mem_budget=0,
+               table=0):
     """Submits every n (at arrivals_s[i] seconds after the start if given,
     else all at once), waits for all answers.  Returns a dict with the
-    answers, per-query latencies (s), throughput and the server's stats."""
+    answers, per-query latencies (s), throughput and the server's stats.
+    With a resident table handle, batches that fit it are planned on it."""
     srv = L.mertens_server_create(device, mem_budget, max_inflight, max_batch)
     try:
+        if table:
+            L.mertens_server_use_table(srv, table)
         tickets = []
         t0 = time.perf_counter()
         if arrivals_s is None:

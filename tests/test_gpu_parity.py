@@ -411,6 +411,74 @@ def test_window_two_word_target_at_1e13():
     assert got_S == {x: v for x, v in want_S.items() if v}
 
 
+# ---- resident M(y) table -------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def table_2e26():
+    t = pm.mertens_table_create(2**26 + 12345, 10**13)
+    yield t
+    pm.mertens_table_destroy(t)
+
+
+def _run_on_table(table, ns, u=0, block_len=0):
+    plan = pm.mertens_plan_on_table(table, ns, u, block_len)
+    try:
+        pm.mertens_run(plan)
+        res = [pm.mertens_result(plan, i, entries=True) for i in range(len(ns))]
+    finally:
+        pm.mertens_destroy(plan)
+    return res
+
+
+def test_table_lookups_are_the_sieve(table_2e26):
+    """Targets n <= y_max are read from the table: M(n) by the plain table."""
+    info = pm.mertens_table_info(table_2e26)
+    assert info["y_max"] == 2**26 + 12345 and info["n_max"] == 10**13
+    ns = [1, 2, 1000, 10**6 + 3, 2**26, 2**26 + 12345]
+    M = oracle.mertens_table(2**26 + 12345)
+    for n, (m, arr) in zip(ns, _run_on_table(table_2e26, ns)):
+        assert m == M[n] and len(arr) == 1, n
+
+
+@pytest.mark.parametrize("n,block_len", [
+    (10**12, 0), (10**12 + 12345, 2**22), (7 * 10**12 + 1, 2**20 + 2048), (2**26 + 12346, 0),
+    (10**13, 0),
+])
+def test_plans_on_table_match_oracle(table_2e26, n, block_len):
+    (m, arr), = _run_on_table(table_2e26, [n], 0, block_len)
+    u = min(n, 2**26 + 12346)
+    assert len(arr) == n // u
+    assert np.array_equal(arr, oracle.mertens_array(n, n // u, L=10**8))
+    # and a sieving plan with the same u agrees
+    m2, arr2 = gpu_array(n, u)
+    assert m == m2 and np.array_equal(arr, arr2)
+
+
+def test_batch_on_table_same_as_alone(table_2e26):
+    ns = [10**12 + 7, 3 * 10**11, 5 * 10**7, 10**13, 123_456_789_012]
+    batch = _run_on_table(table_2e26, ns)
+    for n, (m, arr) in zip(ns, batch):
+        (m1, arr1), = _run_on_table(table_2e26, [n])
+        assert m == m1 and np.array_equal(arr, arr1), n
+
+
+def test_table_refuses_what_it_cannot_serve(table_2e26):
+    with pytest.raises(pm.MertensError) as ei:
+        pm.mertens_plan_on_table(table_2e26, [10**13 + 1])      # above n_max
+    assert ei.value.code == pm.MERTENS_ENOTSUP
+    small = pm.mertens_table_create(10**5, 10**12)
+    try:
+        with pytest.raises(pm.MertensError) as ei:
+            pm.mertens_plan_on_table(small, [10**12])           # sqrt(n) > y_max
+        assert ei.value.code == pm.MERTENS_ENOTSUP
+        with pytest.raises(pm.MertensError):
+            pm.mertens_plan_on_table(small, [10**9], 0, 1000)   # block not a multiple of 2048
+        (m, _), = _run_on_table(small, [10**9])
+        assert m == oracle.mertens(10**9, L=10**6)
+    finally:
+        pm.mertens_table_destroy(small)
+
+
 # ---- full size: n = 10^16, u = 4e10, block 2^28 ------------------------------
 
 def test_table1_1e16_full_configuration(table1):

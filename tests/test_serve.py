@@ -38,6 +38,22 @@ def test_mixed_stream_same_alone_and_in_the_mix():
     assert res["answers"][-1] == oracle.mertens(10**12, L=10**8)
 
 
+def test_server_on_resident_table_same_answers():
+    """With a resident table attached, batches are planned on it (no sieve);
+    answers equal each query alone without a table; targets above the
+    table's n_max still get ordinary plans."""
+    rng = np.random.default_rng(23)
+    ns = [int(10 ** e) for e in rng.uniform(6, 13, size=40)] + [10**13 + 5, 3, 10**6]
+    table = pm.mertens_table_create(2**27, 10**13)
+    try:
+        res = serve.run_stream(ns, max_inflight=4, max_batch=8, table=table)
+    finally:
+        pm.mertens_table_destroy(table)
+    assert res["stats"]["answered"] == len(ns) and res["stats"]["failed"] == 0
+    for n, m in zip(ns, res["answers"]):
+        assert m == pm.mertens(n), n
+
+
 def test_open_loop_poisson_arrivals():
     t, n = workloads.serving_stream(seed=5, count=30, lo_exp=8.0, hi_exp=12.0, rate_per_s=200.0)
     res = serve.run_stream(list(n), arrivals_s=t, max_inflight=3, max_batch=16)
