@@ -310,6 +310,29 @@ int mertens_get_tuning(mertens_tuning *t);
 int mertens_autotune(const mertens_u128 *n, size_t count, int runs, mertens_tuning *best,
                      double *best_ms);
 
+/*
+ * mertens_scan_extremes -- M(y) for every y in [y_first, y_last] from a known
+ * carry = M(y_first - 1), by the sieve and prefix scan (Sec. 3), reduced to
+ * the extremes of M(y) and of M(y)/sqrt(y) over the interval (the scan of
+ * Sec. 6 around a candidate for a new extreme value).  Ratios are compared
+ * exactly (M1^2 y2 against M2^2 y1 in 128 bits); ties go to the smallest y.
+ * 1 <= y_first <= y_last < 2^62.  Runs on `stream`, returns when done; all
+ * scratch (about 2 GB for intervals of 2^30 y or more) is allocated through
+ * the allocator hook and freed before returning.
+ * Errors: MERTENS_EINVAL, MERTENS_ENOTSUP (intervals of 2^46 y or more),
+ * MERTENS_ENOMEM, MERTENS_ECUDA.
+ */
+typedef struct {
+    int64_t M_last;               /* M(y_last)                                  */
+    int64_t M_max, M_min;         /* largest and smallest M(y) ...              */
+    uint64_t y_M_max, y_M_min;    /* ... and where                              */
+    int64_t R_max_M, R_min_M;     /* M(y) at the largest and smallest M/sqrt(y) */
+    uint64_t y_R_max, y_R_min;    /* ... and where                              */
+    double R_max, R_min;          /* those two ratios, rounded to double        */
+} mertens_extremes;
+int mertens_scan_extremes(uint64_t y_first, uint64_t y_last, int64_t carry,
+                          mertens_extremes *out, void *stream);
+
 /* ---- serving: continuous batching of M(n) queries ---------------------- */
 
 /*

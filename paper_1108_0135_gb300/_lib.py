@@ -61,8 +61,16 @@ EXPORTS = [
     "mertens_server_wait", "mertens_server_times", "mertens_server_stats_get",
     "mertens_server_destroy", "mertens_plan_window", "mertens_window_result",
     "mertens_table_create", "mertens_table_info", "mertens_plan_on_table", "mertens_table_destroy",
-    "mertens_server_use_table",
+    "mertens_server_use_table", "mertens_scan_extremes",
 ]
+
+
+class mertens_extremes(ctypes.Structure):
+    _fields_ = [("M_last", ctypes.c_int64), ("M_max", ctypes.c_int64), ("M_min", ctypes.c_int64),
+                ("y_M_max", ctypes.c_uint64), ("y_M_min", ctypes.c_uint64),
+                ("R_max_M", ctypes.c_int64), ("R_min_M", ctypes.c_int64),
+                ("y_R_max", ctypes.c_uint64), ("y_R_min", ctypes.c_uint64),
+                ("R_max", ctypes.c_double), ("R_min", ctypes.c_double)]
 
 
 class mertens_tuning(ctypes.Structure):
@@ -120,6 +128,8 @@ def load():
         lib.mertens_plan_on_table.restype = c_int
         lib.mertens_server_use_table.argtypes = [P, P]
         lib.mertens_server_use_table.restype = c_int
+        lib.mertens_scan_extremes.argtypes = [u64, u64, i64, ctypes.POINTER(mertens_extremes), P]
+        lib.mertens_scan_extremes.restype = c_int
         lib.mertens_table_destroy.argtypes = [P]
         lib.mertens_table_destroy.restype = None
         lib.mertens_run.argtypes = [P, P]
@@ -284,6 +294,15 @@ def mertens_plan_on_table(table: int, n, u: int = 0, block_len: int = 0) -> int:
 
 def mertens_server_use_table(srv: int, table: int) -> None:
     _check(load().mertens_server_use_table(srv, table), "mertens_server_use_table")
+
+
+def mertens_scan_extremes(y_first: int, y_last: int, carry: int, stream=None) -> dict:
+    """Extremes of M(y) and M(y)/sqrt(y) for y in [y_first, y_last], given
+    carry = M(y_first - 1)."""
+    e = mertens_extremes()
+    _check(load().mertens_scan_extremes(int(y_first), int(y_last), int(carry), ctypes.byref(e),
+                                        _stream(stream)), "mertens_scan_extremes")
+    return {name: getattr(e, name) for name, _ in mertens_extremes._fields_}
 
 
 def mertens_table_destroy(table: int) -> None:

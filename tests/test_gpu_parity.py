@@ -411,6 +411,81 @@ def test_window_two_word_target_at_1e13():
     assert got_S == {x: v for x, v in want_S.items() if v}
 
 
+# ---- interval scan: extremes of M(y) and M(y)/sqrt(y) ---------------------------
+
+def _extremes_host(y1, M):
+    """Exact extremes of M(y) and M(y)/sqrt(y), y = y1 + i (ties: smallest y)."""
+    ys = np.arange(y1, y1 + len(M), dtype=np.int64)
+    out = {"M_max": int(M.max()), "y_M_max": int(ys[np.argmax(M)]),
+           "M_min": int(M.min()), "y_M_min": int(ys[np.argmin(M)])}
+    R = M / np.sqrt(ys.astype(np.float64))
+    for key, best in (("max", np.max(R)), ("min", np.min(R))):
+        cand = np.nonzero(np.abs(R - best) <= 1e-9 * max(1.0, abs(best)))[0]
+        pick = None
+        for i in cand:
+            m, y = int(M[i]), int(ys[i])
+            if pick is None:
+                pick = (m, y)
+                continue
+            pm_, py = pick
+            # exact: m/sqrt(y) vs pm_/sqrt(py), by signs and squares
+            a = (m > 0) - (m < 0)
+            b = (pm_ > 0) - (pm_ < 0)
+            if a != b:
+                better = a > b if key == "max" else a < b
+            else:
+                l, r = m * m * py, pm_ * pm_ * y
+                gt = l > r if a >= 0 else l < r       # m/sqrt(y) > pm_/sqrt(py)
+                lt = l < r if a >= 0 else l > r
+                better = gt if key == "max" else lt
+                if l == r:
+                    better = y < py
+            if better:
+                pick = (m, y)
+        out["R_%s_M" % key], out["y_R_%s" % key] = pick
+    return out
+
+
+@pytest.mark.parametrize("y1,length", [(1, 2_000_000), (10**9 + 7, 3 * 10**6 + 11)])
+def test_scan_extremes_against_oracle(y1, length):
+    carry = 0 if y1 == 1 else oracle.mertens(y1 - 1, L=10**6)
+    M = carry + np.cumsum(oracle.mu_window(y1, length).astype(np.int64))
+    got = pm.mertens_scan_extremes(y1, y1 + length - 1, carry)
+    want = _extremes_host(y1, M)
+    assert got["M_last"] == int(M[-1])
+    for k, v in want.items():
+        assert got[k] == v, k
+
+
+def test_scan_finds_the_sec1_extreme():
+    """Sec. 1: |M(n)|/sqrt(n) = 0.570591 at n = 7766842813 (the largest
+    value known before the paper): the scan of 10^6 y either side finds it."""
+    n = 7766842813
+    a, b = n - 10**6, n + 10**6
+    got = pm.mertens_scan_extremes(a, b, oracle.mertens(a - 1, L=10**6))
+    ratio, y = max((abs(got["R_max"]), got["y_R_max"]), (abs(got["R_min"]), got["y_R_min"]))
+    assert y == n and round(ratio, 6) == 0.570591
+
+
+def test_scan_over_blocks_is_consistent():
+    """Ten sieve blocks of 2^30 y from y = 1: M_last is M(10^10) (oracle), and
+    two halves, the second from the first one's M_last, give the same
+    extremes as the whole."""
+    y2 = 10**10
+    whole = pm.mertens_scan_extremes(1, y2, 0)
+    assert whole["M_last"] == oracle.mertens(y2, L=10**7)
+    cut = 3 * 2**30 + 12345
+    h1 = pm.mertens_scan_extremes(1, cut, 0)
+    h2 = pm.mertens_scan_extremes(cut + 1, y2, h1["M_last"])
+    assert h2["M_last"] == whole["M_last"]
+    assert whole["M_max"] == max(h1["M_max"], h2["M_max"])
+    assert whole["M_min"] == min(h1["M_min"], h2["M_min"])
+    best = max((h1["R_max"], h1["y_R_max"]), (h2["R_max"], h2["y_R_max"]))
+    assert whole["y_R_max"] == best[1]
+    worst = min((h1["R_min"], h1["y_R_min"]), (h2["R_min"], h2["y_R_min"]))
+    assert whole["y_R_min"] == worst[1]
+
+
 # ---- resident M(y) table -------------------------------------------------------
 
 @pytest.fixture(scope="module")
