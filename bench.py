@@ -393,7 +393,8 @@ def run_native(args, world, rank, local):
     phases = {"mu_sieve": stats["sieve_ms"], "seg_carry": stats["scan_ms"],
               "update_dense": stats["dense_ms"], "update_gathered": stats["gather_ms"],
               "resolve": stats["resolve_ms"]}
-    roofs = rooflines(phases, stats, peaks, int(stats["blocks"]))
+    ipk = pm.mertens_probe_int_peaks(stream)
+    roofs = rooflines(phases, stats, peaks, int(stats["blocks"]), ipk)
     dom = max(roofs, key=lambda k: phases[k])
     roof = roofs[dom]
 
@@ -506,40 +507,43 @@ TRAFFIC_PER_LAUNCH = {
 SIX_OVER_PI2 = 6.0 / math.pi ** 2
 
 
-def rooflines(phases, stats, peaks, nblocks):
+def rooflines(phases, stats, peaks, nblocks, ipk):
     """Roofline records per kernel class of the timed region.
 
-    All classes here are bound by 32-bit integer issue (no tensor cores, no
-    floating point; HBM traffic is 2 B per sieved y).  The peak is derived
-    from unit counts and the clock: 152 SMs x 64 integer lanes per SM per
-    clock (the IMAD and ALU pipes each retire 64 lanes/clock/SM on GB300,
-    which an integer probe reproduced: 68 and 65) x the maximum SM clock.
-    Algorithmic integer operations per unit:
-      mu_sieve (fused a1+a2): one per sieve update (y, p | y or p^2 | y for
-        every sieving prime p) plus two per y (decision + scan add);
-      update_dense: four 32-bit multiplies per squarefree term (the
-        64x64->128 multiply-high of the quotient), squarefree terms =
-        (6/pi^2) x dense y-range;
-      update_gathered: four per gathered term (same multiply-high)."""
+    Every class here is bound by integer issue (no tensor cores, no floating
+    point; HBM traffic is ~2 B per sieved y).  Denominators are measured on
+    this device by mertens_probe_int_peaks (ipk):
+      update_dense, update_gathered: the update's inner step acc +=
+        mulhi64(m, 2k) >> l, in terms/s (the 64x64 multiply-high runs on the
+        FMA-heavy pipe; ncu shows that pipe as the limiter of both kernels).
+        Algorithmic terms: squarefree y of the dense ranges ((6/pi^2) x the
+        summed dense y-range) and one per gathered j.
+      mu_sieve: 32-bit ALU lane operations/s (LOP3 + IADD3 chains).
+        Algorithmic operations: one per sieve update (y, p | y or p^2 | y
+        for every sieving prime p) plus two per y (decision + scan add)."""
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    peak = 152 * 64 * sm_mhz * 1e6 / 1e12  # T int-op/s
-    ops = {
-        "mu_sieve": stats["sieve_updates"] + 2.0 * stats["y_sieved"],
-        "update_dense": 4.0 * SIX_OVER_PI2 * stats["dense_y"],
-        "update_gathered": 4.0 * stats["gather_j"],
+    mulhi_peak = ipk["mulhi_terms_per_s"] / 1e12
+    alu_peak = 2.0 * ipk["alu_pairs_per_s"] / 1e12
+    work = {
+        "mu_sieve": (stats["sieve_updates"] + 2.0 * stats["y_sieved"], alu_peak, "T int-op/s",
+                     "measured: LOP3+IADD3 chains on all SMs, 2 ops per pair"),
+        "update_dense": (SIX_OVER_PI2 * stats["dense_y"], mulhi_peak, "T mulhi-terms/s",
+                         "measured: acc += mulhi64(m,2k) >> l chains on all SMs"),
+        "update_gathered": (float(stats["gather_j"]), mulhi_peak, "T mulhi-terms/s",
+                            "measured: acc += mulhi64(m,2k) >> l chains on all SMs"),
     }
     launches = {"mu_sieve": nblocks, "update_dense": 1, "update_gathered": nblocks}
     out = {}
-    for k, v in ops.items():
+    for k, (v, peak, unit, src) in work.items():
         ms = phases.get(k, 0.0)
         if ms <= 0:
             continue
         achieved = v / (ms / 1e3) / 1e12
         out[k] = {"bound": "alu", "kernel": k, "achieved": achieved, "peak": peak,
-                  "unit": "T int-op/s", "frac": achieved / peak,
+                  "unit": unit, "frac": achieved / peak,
                   "traffic": TRAFFIC_PER_LAUNCH.get(k),
                   "launches_per_step": launches[k],
-                  "peak_source": f"derived: 152 SM x 64 int lanes/clk x {sm_mhz:.0f} MHz"}
+                  "peak_source": f"{src} ({ipk['sms']} SMs, max SM clock {sm_mhz:.0f} MHz)"}
     return out
 
 

@@ -61,7 +61,7 @@ EXPORTS = [
     "mertens_server_wait", "mertens_server_times", "mertens_server_stats_get",
     "mertens_server_destroy", "mertens_plan_window", "mertens_window_result",
     "mertens_table_create", "mertens_table_info", "mertens_plan_on_table", "mertens_table_destroy",
-    "mertens_server_use_table", "mertens_scan_extremes",
+    "mertens_server_use_table", "mertens_scan_extremes", "mertens_probe_int_peaks",
 ]
 
 
@@ -71,6 +71,11 @@ class mertens_extremes(ctypes.Structure):
                 ("R_max_M", ctypes.c_int64), ("R_min_M", ctypes.c_int64),
                 ("y_R_max", ctypes.c_uint64), ("y_R_min", ctypes.c_uint64),
                 ("R_max", ctypes.c_double), ("R_min", ctypes.c_double)]
+
+
+class mertens_int_peaks(ctypes.Structure):
+    _fields_ = [("mulhi_terms_per_s", ctypes.c_double), ("imad32_per_s", ctypes.c_double),
+                ("alu_pairs_per_s", ctypes.c_double), ("sms", ctypes.c_int)]
 
 
 class mertens_tuning(ctypes.Structure):
@@ -130,6 +135,8 @@ def load():
         lib.mertens_server_use_table.restype = c_int
         lib.mertens_scan_extremes.argtypes = [u64, u64, i64, ctypes.POINTER(mertens_extremes), P]
         lib.mertens_scan_extremes.restype = c_int
+        lib.mertens_probe_int_peaks.argtypes = [ctypes.POINTER(mertens_int_peaks), P]
+        lib.mertens_probe_int_peaks.restype = c_int
         lib.mertens_table_destroy.argtypes = [P]
         lib.mertens_table_destroy.restype = None
         lib.mertens_run.argtypes = [P, P]
@@ -303,6 +310,14 @@ def mertens_scan_extremes(y_first: int, y_last: int, carry: int, stream=None) ->
     _check(load().mertens_scan_extremes(int(y_first), int(y_last), int(carry), ctypes.byref(e),
                                         _stream(stream)), "mertens_scan_extremes")
     return {name: getattr(e, name) for name, _ in mertens_extremes._fields_}
+
+
+def mertens_probe_int_peaks(stream=None) -> dict:
+    """Measured integer rates of the current device (roofline denominators)."""
+    r = mertens_int_peaks()
+    _check(load().mertens_probe_int_peaks(ctypes.byref(r), _stream(stream)),
+           "mertens_probe_int_peaks")
+    return {name: getattr(r, name) for name, _ in mertens_int_peaks._fields_}
 
 
 def mertens_table_destroy(table: int) -> None:
