@@ -282,8 +282,9 @@ __global__ void __launch_bounds__(256) sparse_update_kernel(SparseBlockArgs b, S
         const uint64_t jb = (jt - jb0 + 1 > (uint64_t)kSparseItem) ? jt - kSparseItem + 1 : jb0;
         const uint64_t k2 = a.K[e] << 1;
         int64_t acc = 0;
-        for (uint64_t j = jt - lane; j >= jb && j <= jt; j -= 32) {
-            const uint64_t y = div_magic(k2, a.MG[j], magic_shift(j));
+        const uint64_t *mp = a.MG + (jt - lane);
+        for (uint64_t j = jt - lane; j >= jb && j <= jt; j -= 32, mp -= 32) {
+            const uint64_t y = div_magic(k2, *mp, magic_shift(j));
             acc += block_M(a.segoff, a.Mloc, y - b.y1);
         }
         acc = warp_sum_i64(acc);
@@ -363,10 +364,15 @@ __global__ void __launch_bounds__(512) gather_tile_kernel(GatherArgs a)
                 const uint32_t cns = __shfl_sync(0xffffffffu, cnt, src);
                 const uint64_t k2s = __shfl_sync(0xffffffffu, k2, src);
                 int acc = 0;
-                for (uint32_t i = (uint32_t)lane; i < cns; i += 32u) {
-                    const uint32_t j = jts - i;
-                    const uint64_t y = div_magic(k2s, a.MG[j], 32u - __clz(j - 1u));
-                    acc += Mt[(uint32_t)y - t1lo];
+                if ((uint32_t)lane < cns) {
+                    // lanes over j descending, 32 apart; the magic pointer is
+                    // walked rather than indexed (measured faster)
+                    uint32_t j = jts - (uint32_t)lane;
+                    const uint64_t *mp = a.MG + j;
+                    for (uint32_t i = (uint32_t)lane; i < cns; i += 32u, j -= 32u, mp -= 32) {
+                        const uint64_t y = div_magic(k2s, *mp, 32u - __clz(j - 1u));
+                        acc += Mt[(uint32_t)y - t1lo];
+                    }
                 }
                 int64_t tot = warp_sum_i64((int64_t)acc);
                 if (lane == 0) {
