@@ -176,7 +176,9 @@ int mertens_scan_extremes(uint64_t y_first, uint64_t y_last, int64_t carry,
     }
     PrimeTable pt;
     int rc = MERTENS_OK;
-    const int prc = prime_table_create(&pt, al, y_last, s);
+    int prc = prime_table_create(&pt, al, y_last, s);
+    if (prc == 0)
+        prc = sieve_scratch_create(&pt, L);
     if (prc != 0)
         rc = prc == 6 ? MERTENS_ENOTSUP : (prc == 2 ? MERTENS_ENOMEM : MERTENS_ECUDA);
     const uint64_t nseg = sieve_segments(L);
@@ -216,6 +218,10 @@ int mertens_scan_extremes(uint64_t y_first, uint64_t y_last, int64_t carry,
              cudaMemcpyAsync(&last, cy + nblocks, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
              cudaStreamSynchronize(s) != cudaSuccess))
             rc = MERTENS_ECUDA;
+        if (rc == MERTENS_OK && sieve_scratch_status(&pt)) {
+            set_last_error("mertens_scan_extremes: a sieve bucket overflowed its capacity");
+            rc = MERTENS_EOVERFLOW;
+        }
         if (rc == MERTENS_OK) {
             out->M_last = last;
             out->M_max = e.mx;

@@ -40,6 +40,15 @@ struct PrimeTable {
     uint64_t *blk_r2 = nullptr;   // per block: y1 mod p^2
     uint4 *pat8 = nullptr;        // 16 phase copies of the byte pattern
     uint32_t *patsq = nullptr;    // square flags of 4, 9, 25, 49 as a long bit string
+    // persistent byte sieve: p | w(p) << 24 for p < 2^17, and scratch for
+    // blocks of up to scratch_len y (sieve_scratch_create)
+    uint32_t np_mid = 0;          // primes below 2^17
+    uint32_t *pw = nullptr;
+    uint64_t scratch_len = 0;
+    uint32_t bucket_cap = 0;      // entries per tile
+    uint64_t *bucket = nullptr;   // tiles x bucket_cap
+    uint32_t *gsq = nullptr;      // one bit per y of a block, whole tiles
+    uint32_t *perr = nullptr;     // status bits of the persistent kernel
     // host copy of the primes (for counting primes <= a bound)
     uint32_t *host_p = nullptr;
     Allocator al;
@@ -66,6 +75,13 @@ struct SieveLaunch {
 int prime_table_create(PrimeTable *t, const Allocator &al, uint64_t y_max, cudaStream_t s,
                        bool with_bytes = true);
 void prime_table_destroy(PrimeTable *t);
+// Scratch of the persistent byte sieve for blocks of up to max_len y (bucket
+// storage sized from the table's primes above 2^17, and the square bit
+// array).  Optional: without it blocks take the per-tile byte kernel.
+int sieve_scratch_create(PrimeTable *t, uint64_t max_len);
+// Status bits the persistent sieve left since the last call (and clears them):
+// kErrBucket when a bucket overflowed (the block's M(y) is then wrong).
+uint32_t sieve_scratch_status(PrimeTable *t);
 // Number of primes in the table that are <= b.
 uint32_t prime_count_upto(const PrimeTable *t, uint64_t b);
 // Enqueues the fused steps a1 + a2 for one block.  Returns the number of

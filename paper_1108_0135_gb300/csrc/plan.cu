@@ -981,6 +981,8 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
         rc = MERTENS_ENOMEM;
     if (rc == MERTENS_OK && !table) {
         int prc = prime_table_create(&p->pt, p->al, std::max<uint64_t>(p->y_last, 1), nullptr);
+        if (prc == 0)
+            prc = sieve_scratch_create(&p->pt, block_len);
         if (prc != 0)
             rc = prc == 6 ? MERTENS_ENOTSUP : (prc == 2 ? MERTENS_ENOMEM : MERTENS_ECUDA);
     }
@@ -1481,6 +1483,10 @@ int mertens_result(mertens_plan_t p, size_t i, int64_t *M_n, int64_t *entries, s
         set_last_error("mertens_result: |M(y)| exceeded the int32 block type");
         return MERTENS_EOVERFLOW;
     }
+    if (!p->table && sieve_scratch_status(&p->pt)) {
+        set_last_error("mertens_result: a sieve bucket overflowed its capacity");
+        return MERTENS_EOVERFLOW;
+    }
     if (len)
         *len = p->X[i];
     const uint64_t o = p->off[i];
@@ -1543,6 +1549,10 @@ int mertens_window_result(mertens_plan_t p, size_t i, uint64_t *S_loc, uint64_t 
     if (cudaEventSynchronize(p->done) != cudaSuccess) {
         set_last_error("mertens_window_result: %s", cudaGetErrorString(cudaGetLastError()));
         return MERTENS_ECUDA;
+    }
+    if (!p->table && sieve_scratch_status(&p->pt)) {
+        set_last_error("mertens_window_result: a sieve bucket overflowed its capacity");
+        return MERTENS_EOVERFLOW;
     }
     if (len)
         *len = p->X[i];
@@ -1681,6 +1691,8 @@ static int sieve_window(uint64_t y1, uint64_t len, int8_t *mu_dev, int64_t carry
     Allocator al = current_allocator();
     PrimeTable pt;
     int prc = prime_table_create(&pt, al, y1 + len - 1, s);
+    if (prc == 0 && len <= (1ull << 30))
+        prc = sieve_scratch_create(&pt, len);
     if (prc != 0) {
         if (pt.np)
             prime_table_destroy(&pt);
@@ -1719,6 +1731,10 @@ static int sieve_window(uint64_t y1, uint64_t len, int8_t *mu_dev, int64_t carry
             rc = MERTENS_ECUDA;
         if (rc == MERTENS_OK && (e & kErrMOverflow))
             rc = MERTENS_EOVERFLOW;
+        if (rc == MERTENS_OK && sieve_scratch_status(&pt)) {
+            set_last_error("sieve: a sieve bucket overflowed its capacity");
+            rc = MERTENS_EOVERFLOW;
+        }
     }
     if (rc == MERTENS_ECUDA)
         set_last_error("sieve: %s", cudaGetErrorString(cudaGetLastError()));

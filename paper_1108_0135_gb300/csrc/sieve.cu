@@ -4,6 +4,7 @@
 // stored as int16 relative to M at the start of each kSegY-segment; a second
 // small kernel turns the segment sums into int64 segment offsets carrying
 // M(y1 - 1) from the previous block.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -306,6 +307,8 @@ struct ByteArgs {
     uint32_t np;          // primes used (all p <= P)
     uint32_t np_piece;    // [4, np_piece): p < 128, sieved in eighth-tile pieces
     uint32_t np_small;    // [np_piece, np_small): p < 2048, a warp per prime
+    uint32_t np_mid;      // persistent kernel: [np_small, np_mid) p < 2^17, [np_mid, np) above
+    uint32_t cap;         // persistent kernel: bucket entries per tile
     float scale;          // S: w(p) = odd integer nearest S log2 p
     float thr_half;       // (S/2) log2 P
     const uint4 *pq;
@@ -317,6 +320,11 @@ struct ByteArgs {
     int32_t *segsum;
     int8_t *mu_out;
     uint64_t mu_base, mu_end;
+    // persistent kernel only
+    const uint32_t *pw;   // p | w(p) << 24 for p < 2^17
+    const uint32_t *gsq;  // square flags of primes >= 2048 over the block (one bit per y)
+    uint64_t *bucket;     // per tile of the block: cap entries (p << 24 | w << 17 | offset)
+    uint32_t *err;        // kErrBucket when a bucket overflows
 };
 
 // Small-prime job (p < 2048): the multiples of p in the tile offsets [lo, hi),
@@ -412,78 +420,13 @@ __device__ __forceinline__ int byte_thr(uint64_t y, float scale, float thr_half)
     return (int)floorf(scale * __log2f(__ull2float_rn(y)) - thr_half);
 }
 
-__global__ void __launch_bounds__(kSieveThreads, 1) mu_sieve_byte_kernel(ByteArgs a)
+// Decode + scan of one byte-sieve tile (shared by the byte kernels): each warp
+// owns two 2048-y segments, 16 y per lane per round (see the comment above
+// ByteArgs for the decision rule).
+__device__ __forceinline__ void byte_tile_decode(const ByteArgs &a, const uint4 *sb,
+                                                 const uint32_t *sq, uint32_t a0, uint64_t t1,
+                                                 uint32_t tl, uint32_t lane, uint32_t warp)
 {
-    extern __shared__ uint4 sb[];
-    uint32_t *w = reinterpret_cast<uint32_t *>(sb);  // kByteWords words, four y each
-    uint32_t *sq = w + kByteWords;                     // kByteSqWords words, 32 y each
-    __shared__ uint32_t s_job;
-    __shared__ uint4 s_jd[kByteJobsMax];
-    const uint32_t a0 = blockIdx.x * (uint32_t)kByteTile;
-    const uint64_t t1 = a.y1 + a0;
-    const uint32_t tl = min(a.len - a0, (uint32_t)kByteTile);
-    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    const uint32_t jp = a.np_piece > 4 ? 8u * (a.np_piece - 4) : 0u;
-    const uint32_t js = jp + (a.np_small - a.np_piece);  // small-prime jobs (<= kByteJobsMax)
-    const uint32_t jobs = js + (a.np - a.np_small + 63u) / 64u;
-
-    // prologue: small-prime job descriptors (a thread each), and the
-    // pre-sieve pattern (bytes of 2, 3, 5, 7, square flags of 4, 9, 25, 49)
-    uint32_t single = kNone;
-    {
-        if (threadIdx.x < js)
-            s_jd[threadIdx.x] = byte_small_desc(a, threadIdx.x, jp, a0, tl, &single);
-        const uint32_t ph = (uint32_t)(t1 % kPatternPeriod);
-        const uint4 *src = a.pat8 + (size_t)(ph & 15u) * (kPat8Len / 16) + (ph >> 4);
-#pragma unroll 4
-        for (uint32_t i = threadIdx.x; i < (uint32_t)kByteTile / 16; i += kSieveThreads)
-            sb[i] = src[i];
-        const uint32_t j0 = ph >> 5, s = ph & 31u;
-        for (uint32_t i = threadIdx.x; i < (uint32_t)kByteSqWords; i += kSieveThreads)
-            sq[i] = __funnelshift_r(a.patsq[j0 + i], a.patsq[j0 + i + 1], s);
-        if (threadIdx.x == 0)
-            s_job = 0;
-    }
-    __syncthreads();
-    if (single != kNone)
-        atomicOr(&sq[single >> 5], 1u << (single & 31u));
-
-    // jobs, largest first, handed out through a shared counter: small-prime
-    // jobs (a warp over the multiples of one prime), then 64 primes >= 2048 at
-    // a time (two per lane, the second one's loads in flight during the first)
-    for (;;) {
-        uint32_t job = 0;
-        if (lane == 0)
-            job = atomicAdd(&s_job, 1u);
-        job = __shfl_sync(0xffffffffu, job, 0);
-        if (job >= jobs)
-            break;
-        if (job < js) {
-            byte_small_job(s_jd[job], w, sq, lane);
-        } else {
-            const uint32_t t0 = a.np_small + (job - js) * 64u + lane, t1p = t0 + 32u;
-            uint4 q0 = make_uint4(0, 0, 0, 0), q1 = q0;
-            uint32_t r0 = 0, r1 = 0;
-            uint64_t r20 = 0, r21 = 0;
-            if (t0 < a.np) {
-                q0 = a.pq[t0];
-                r0 = a.r[t0];
-                r20 = a.r2[t0];
-            }
-            if (t1p < a.np) {
-                q1 = a.pq[t1p];
-                r1 = a.r[t1p];
-                r21 = a.r2[t1p];
-            }
-            if (t0 < a.np)
-                byte_large_prime(q0, r0, r20, w, sq, a0, tl);
-            if (t1p < a.np)
-                byte_large_prime(q1, r1, r21, w, sq, a0, tl);
-        }
-    }
-    __syncthreads();
-
-    // decode + scan: warp owns two segments, 16 y per lane per round
     const bool tile_thr = t1 >= kByteTileThrMin;
     uint32_t bias4 = 0;
     if (tile_thr) {
@@ -581,6 +524,263 @@ __global__ void __launch_bounds__(kSieveThreads, 1) mu_sieve_byte_kernel(ByteArg
         }
         if (lane == 0)
             a.segsum[(a0 + so) >> kSegShift] = run;
+    }
+}
+
+__global__ void __launch_bounds__(kSieveThreads, 1) mu_sieve_byte_kernel(ByteArgs a)
+{
+    extern __shared__ uint4 sb[];
+    uint32_t *w = reinterpret_cast<uint32_t *>(sb);  // kByteWords words, four y each
+    uint32_t *sq = w + kByteWords;                     // kByteSqWords words, 32 y each
+    __shared__ uint32_t s_job;
+    __shared__ uint4 s_jd[kByteJobsMax];
+    const uint32_t a0 = blockIdx.x * (uint32_t)kByteTile;
+    const uint64_t t1 = a.y1 + a0;
+    const uint32_t tl = min(a.len - a0, (uint32_t)kByteTile);
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t jp = a.np_piece > 4 ? 8u * (a.np_piece - 4) : 0u;
+    const uint32_t js = jp + (a.np_small - a.np_piece);  // small-prime jobs (<= kByteJobsMax)
+    const uint32_t jobs = js + (a.np - a.np_small + 63u) / 64u;
+
+    // prologue: small-prime job descriptors (a thread each), and the
+    // pre-sieve pattern (bytes of 2, 3, 5, 7, square flags of 4, 9, 25, 49)
+    uint32_t single = kNone;
+    {
+        if (threadIdx.x < js)
+            s_jd[threadIdx.x] = byte_small_desc(a, threadIdx.x, jp, a0, tl, &single);
+        const uint32_t ph = (uint32_t)(t1 % kPatternPeriod);
+        const uint4 *src = a.pat8 + (size_t)(ph & 15u) * (kPat8Len / 16) + (ph >> 4);
+#pragma unroll 4
+        for (uint32_t i = threadIdx.x; i < (uint32_t)kByteTile / 16; i += kSieveThreads)
+            sb[i] = src[i];
+        const uint32_t j0 = ph >> 5, s = ph & 31u;
+        for (uint32_t i = threadIdx.x; i < (uint32_t)kByteSqWords; i += kSieveThreads)
+            sq[i] = __funnelshift_r(a.patsq[j0 + i], a.patsq[j0 + i + 1], s);
+        if (threadIdx.x == 0)
+            s_job = 0;
+    }
+    __syncthreads();
+    if (single != kNone)
+        atomicOr(&sq[single >> 5], 1u << (single & 31u));
+
+    // jobs, largest first, handed out through a shared counter: small-prime
+    // jobs (a warp over the multiples of one prime), then 64 primes >= 2048 at
+    // a time (two per lane, the second one's loads in flight during the first)
+    for (;;) {
+        uint32_t job = 0;
+        if (lane == 0)
+            job = atomicAdd(&s_job, 1u);
+        job = __shfl_sync(0xffffffffu, job, 0);
+        if (job >= jobs)
+            break;
+        if (job < js) {
+            byte_small_job(s_jd[job], w, sq, lane);
+        } else {
+            const uint32_t t0 = a.np_small + (job - js) * 64u + lane, t1p = t0 + 32u;
+            uint4 q0 = make_uint4(0, 0, 0, 0), q1 = q0;
+            uint32_t r0 = 0, r1 = 0;
+            uint64_t r20 = 0, r21 = 0;
+            if (t0 < a.np) {
+                q0 = a.pq[t0];
+                r0 = a.r[t0];
+                r20 = a.r2[t0];
+            }
+            if (t1p < a.np) {
+                q1 = a.pq[t1p];
+                r1 = a.r[t1p];
+                r21 = a.r2[t1p];
+            }
+            if (t0 < a.np)
+                byte_large_prime(q0, r0, r20, w, sq, a0, tl);
+            if (t1p < a.np)
+                byte_large_prime(q1, r1, r21, w, sq, a0, tl);
+        }
+    }
+    __syncthreads();
+
+    byte_tile_decode(a, sb, sq, a0, t1, tl, lane, warp);
+}
+
+// ---------------------------------------------------------------------------
+// a1 + a2, persistent byte variant for blocks with many large primes.  One
+// CTA per SM takes a contiguous range of tiles of the block and keeps, across
+// its tiles:
+//   * for every prime 2048 <= p < 2^17 (at most two tiles' worth of hits per
+//     tile), the offset of its next multiple, in shared memory -- no division
+//     per (prime, tile);
+//   * for every prime p >= 2^17 (at most one hit per tile), a bucket entry in
+//     the tile of its next multiple (Oliveira e Silva's bucket sieve, here per
+//     CTA): a tile visits only the primes that hit it and forwards each to the
+//     tile of its next multiple.
+// Multiples of p^2 for p >= 2048 come from a bit array over the block made by
+// square_bits_kernel; primes below 2048 are set up per tile as in the byte
+// kernel.  The tile's bytes, decode and scan are those of the byte kernel.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kMedMax = 12288;          // primes in [2048, 2^17): 11942
+constexpr uint32_t kPersistTilesMax = 128;   // tiles per CTA (blocks <= 2^30 y, >= 64 CTAs)
+constexpr uint32_t kBucketJob = 256;         // bucket entries per job (8 per lane)
+constexpr uint32_t kErrBucket = 4u;
+
+__device__ __forceinline__ uint64_t bucket_entry(uint32_t p, uint32_t w, uint32_t off)
+{
+    return ((uint64_t)p << 24) | ((uint64_t)w << 17) | off;
+}
+
+// Bits of y (offset from the block start) with q^2 | y for a prime
+// 2048 <= q <= P: one thread per prime walks its square multiples.
+__global__ void square_bits_kernel(uint32_t len, uint32_t p0, uint32_t np,
+                                   const uint32_t *__restrict__ p, const uint64_t *__restrict__ r2,
+                                   uint32_t *__restrict__ bits)
+{
+    const uint32_t t = p0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= np)
+        return;
+    const uint64_t q = p[t], q2 = q * q;
+    const uint64_t rem = r2[t];
+    for (uint64_t o = rem ? q2 - rem : 0; o < len; o += q2)
+        atomicOr(&bits[o >> 5], 1u << (o & 31u));
+}
+
+__global__ void __launch_bounds__(kSieveThreads, 1) mu_sieve_persist_kernel(ByteArgs a)
+{
+    extern __shared__ uint4 sb[];
+    uint32_t *w = reinterpret_cast<uint32_t *>(sb);  // kByteWords words, four y each
+    uint32_t *sq = w + kByteWords;                     // kByteSqWords words, 32 y each
+    uint32_t *moff = sq + kByteSqWords;                // kMedMax next offsets
+    __shared__ uint32_t s_job;
+    __shared__ uint4 s_jd[kByteJobsMax];
+    __shared__ uint32_t s_cnt[kPersistTilesMax];
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t ntiles = (a.len + kByteTile - 1) / kByteTile;
+    const uint32_t tb = (uint32_t)((uint64_t)blockIdx.x * ntiles / gridDim.x);
+    const uint32_t te = (uint32_t)((uint64_t)(blockIdx.x + 1) * ntiles / gridDim.x);
+    const uint32_t T = te - tb;  // tiles of this CTA (the host keeps it <= kPersistTilesMax)
+    if (T == 0)
+        return;
+    const uint32_t A0 = tb * (uint32_t)kByteTile;
+    const uint32_t nmed = a.np_mid - a.np_small;
+
+    // CTA prologue: next multiple of every medium prime, buckets of the large
+    for (uint32_t i = threadIdx.x; i < kPersistTilesMax; i += kSieveThreads)
+        s_cnt[i] = 0;
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < nmed; i += kSieveThreads) {
+        const uint32_t t = a.np_small + i;
+        const uint4 q = a.pq[t];
+        const uint32_t v = a.r[t] + A0;  // < 2^31
+        const uint32_t rem = v - div_magic32(v, q.y, q.w & 255u) * q.x;
+        moff[i] = rem ? q.x - rem : 0u;
+    }
+    for (uint32_t t = a.np_mid + threadIdx.x; t < a.np; t += kSieveThreads) {
+        const uint4 q = a.pq[t];
+        const uint32_t v = a.r[t] + A0;  // < 2^31
+        const uint32_t rem = v - div_magic32(v, q.y, q.w & 255u) * q.x;
+        const uint32_t off = rem ? q.x - rem : 0u;  // < p < 2^27
+        const uint32_t tr = off >> 17;
+        if (tr < T) {
+            const uint32_t slot = atomicAdd(&s_cnt[tr], 1u);
+            if (slot < a.cap)
+                a.bucket[(size_t)(tb + tr) * a.cap + slot] =
+                    bucket_entry(q.x, q.w >> 16, off & (kByteTile - 1));
+            else
+                atomicOr(a.err, kErrBucket);
+        }
+    }
+    __syncthreads();
+
+    const uint32_t jp = a.np_piece > 4 ? 8u * (a.np_piece - 4) : 0u;
+    const uint32_t js = jp + (a.np_small - a.np_piece);  // small-prime jobs
+    const uint32_t jm = js + (nmed + 63u) / 64u;          // + medium jobs (64 primes)
+    for (uint32_t tt = 0; tt < T; ++tt) {
+        const uint32_t a0 = A0 + tt * (uint32_t)kByteTile;
+        const uint64_t t1 = a.y1 + a0;
+        const uint32_t tl = min(a.len - a0, (uint32_t)kByteTile);
+        const uint32_t nb = min(s_cnt[tt], a.cap);  // final: appends go to later tiles
+        const uint32_t jobs = jm + (nb + kBucketJob - 1) / kBucketJob;
+        uint32_t single = kNone;
+        {
+            if (threadIdx.x < js)
+                s_jd[threadIdx.x] = byte_small_desc(a, threadIdx.x, jp, a0, tl, &single);
+            const uint32_t ph = (uint32_t)(t1 % kPatternPeriod);
+            const uint4 *src = a.pat8 + (size_t)(ph & 15u) * (kPat8Len / 16) + (ph >> 4);
+#pragma unroll 4
+            for (uint32_t i = threadIdx.x; i < (uint32_t)kByteTile / 16; i += kSieveThreads)
+                sb[i] = src[i];
+            const uint32_t j0 = ph >> 5, sh = ph & 31u;
+            const uint32_t *gs = a.gsq + (a0 >> 5);
+            for (uint32_t i = threadIdx.x; i < (uint32_t)kByteSqWords; i += kSieveThreads)
+                sq[i] = __funnelshift_r(a.patsq[j0 + i], a.patsq[j0 + i + 1], sh) | gs[i];
+            if (threadIdx.x == 0)
+                s_job = 0;
+        }
+        __syncthreads();
+        if (single != kNone)
+            atomicOr(&sq[single >> 5], 1u << (single & 31u));
+        for (;;) {
+            uint32_t job = 0;
+            if (lane == 0)
+                job = atomicAdd(&s_job, 1u);
+            job = __shfl_sync(0xffffffffu, job, 0);
+            if (job >= jobs)
+                break;
+            if (job < js) {
+                byte_small_job(s_jd[job], w, sq, lane);
+            } else if (job < jm) {
+                // 64 medium primes, two per lane, offsets carried in shared memory
+#pragma unroll
+                for (uint32_t h = 0; h < 2; ++h) {
+                    const uint32_t i = (job - js) * 64u + h * 32u + lane;
+                    if (i < nmed) {
+                        const uint32_t pwv = a.pw[a.np_small + i];
+                        const uint32_t p = pwv & 0xffffffu, wt = pwv >> 24;
+                        uint32_t yo = moff[i];
+                        for (; yo < tl; yo += p)
+                            atomicAdd(&w[yo >> 2], __funnelshift_l(0u, wt, yo << 3));
+                        moff[i] = yo - (uint32_t)kByteTile;
+                    }
+                }
+            } else {
+                // bucket entries of this tile: mark, forward to the tile of the
+                // next multiple (warp-aggregated slot allocation)
+                const uint32_t e0 = (job - jm) * kBucketJob;
+                uint64_t *bk = a.bucket + (size_t)(tb + tt) * a.cap;
+#pragma unroll 1
+                for (uint32_t k = 0; k < kBucketJob / 32u; ++k) {
+                    const uint32_t e = e0 + k * 32u + lane;
+                    uint32_t nt = 0xffffffffu, fwd = 0;
+                    uint64_t ent = 0;
+                    if (e < nb) {
+                        ent = bk[e];
+                        const uint32_t off = (uint32_t)ent & (kByteTile - 1);
+                        const uint32_t wt = (uint32_t)(ent >> 17) & 127u;
+                        const uint32_t p = (uint32_t)(ent >> 24);
+                        atomicAdd(&w[off >> 2], __funnelshift_l(0u, wt, off << 3));
+                        const uint32_t nx = off + p;
+                        if (tt + (nx >> 17) < T) {
+                            nt = tt + (nx >> 17);
+                            fwd = nx & (kByteTile - 1);
+                        }
+                    }
+                    const uint32_t peers = __match_any_sync(0xffffffffu, nt);
+                    if (nt != 0xffffffffu) {
+                        const uint32_t leader = __ffs(peers) - 1u;
+                        uint32_t base = 0;
+                        if (lane == leader)
+                            base = atomicAdd(&s_cnt[nt], (uint32_t)__popc(peers));
+                        base = __shfl_sync(peers, base, leader);
+                        const uint32_t slot = base + __popc(peers & ((1u << lane) - 1u));
+                        if (slot < a.cap)
+                            a.bucket[(size_t)(tb + nt) * a.cap + slot] =
+                                (ent & ~(uint64_t)(kByteTile - 1)) | fwd;
+                        else
+                            atomicOr(a.err, kErrBucket);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        byte_tile_decode(a, sb, sq, a0, t1, tl, lane, warp);
+        __syncthreads();  // the next tile reuses the shared arrays
     }
 }
 
@@ -695,6 +895,18 @@ static int byte_tables_create(PrimeTable *t, const std::vector<uint32_t> &pr, cu
     for (uint32_t j = 0; j < 32u * kPatSqWords; ++j)
         if (sqp[j % kPatternPeriod])
             psq[j >> 5] |= 1u << (j & 31u);
+    // p | w << 24 for the primes below 2^17
+    uint32_t nmid = 0;
+    while (nmid < np && pr[nmid] < (1u << 17))
+        ++nmid;
+    t->np_mid = nmid;
+    std::vector<uint32_t> pwv(nmid + 1, 0u);
+    for (uint32_t i = 0; i < nmid; ++i)
+        pwv[i] = pr[i] | (byte_weight(pr[i], t->byte_scale) << 24);
+    t->pw = (uint32_t *)dev_alloc(t->al, (nmid + 1) * 4);
+    if (!t->pw)
+        return 2;
+    cudaMemcpyAsync(t->pw, pwv.data(), (nmid + 1) * 4, cudaMemcpyHostToDevice, s);
     t->pq = (uint4 *)dev_alloc(t->al, np * sizeof(uint4));
     t->blk_r2 = (uint64_t *)dev_alloc(t->al, np * 8);
     t->pat8 = (uint4 *)dev_alloc(t->al, p8.size());
@@ -794,6 +1006,14 @@ void prime_table_destroy(PrimeTable *t)
     dev_free(t->al, t->blk_r2, np * 8);
     dev_free(t->al, t->pat8, (size_t)16 * kPat8Len);
     dev_free(t->al, t->patsq, kPatSqWords * 4);
+    if (t->pw)
+        dev_free(t->al, t->pw, ((size_t)t->np_mid + 1) * 4);
+    if (t->scratch_len) {
+        const uint64_t ntiles = (t->scratch_len + kByteTile - 1) / kByteTile;
+        dev_free(t->al, t->bucket, ntiles * t->bucket_cap * 8);
+        dev_free(t->al, t->gsq, ntiles * (kByteTile / 8));
+        dev_free(t->al, t->perr, 4);
+    }
     free(t->host_p);
     *t = PrimeTable();
 }
@@ -809,6 +1029,47 @@ uint32_t prime_count_upto(const PrimeTable *t, uint64_t b)
             hi = mid;
     }
     return lo;
+}
+
+int sieve_scratch_create(PrimeTable *t, uint64_t max_len)
+{
+    if (!t->pq || t->scratch_len || max_len == 0 || max_len > (1ull << 30))
+        return 0;
+    // entries of a tile: the primes p > 2^17 whose next multiple falls in it,
+    // one with probability 2^17/p: mean mu, at most mu + 10 sqrt(mu) + 256
+    double mu = 0;
+    for (uint32_t i = t->np_mid; i < t->np; ++i)
+        mu += (double)kByteTile / (double)t->host_p[i];
+    uint32_t cap = (uint32_t)(mu + 10.0 * std::sqrt(mu) + 256.0);
+    cap = (cap + 31u) & ~31u;
+    const uint64_t ntiles = (max_len + kByteTile - 1) / kByteTile;
+    t->bucket = (uint64_t *)dev_alloc(t->al, ntiles * cap * 8);
+    t->gsq = (uint32_t *)dev_alloc(t->al, ntiles * (kByteTile / 8));
+    t->perr = (uint32_t *)dev_alloc(t->al, 4);
+    if (!t->bucket || !t->gsq || !t->perr) {
+        dev_free(t->al, t->bucket, ntiles * cap * 8);
+        dev_free(t->al, t->gsq, ntiles * (kByteTile / 8));
+        dev_free(t->al, t->perr, 4);
+        t->bucket = nullptr;
+        t->gsq = nullptr;
+        t->perr = nullptr;
+        return 2;
+    }
+    cudaMemset(t->perr, 0, 4);
+    t->bucket_cap = cap;
+    t->scratch_len = max_len;
+    return 0;
+}
+
+uint32_t sieve_scratch_status(PrimeTable *t)
+{
+    if (!t->perr)
+        return 0;
+    uint32_t v = 0;
+    cudaMemcpy(&v, t->perr, 4, cudaMemcpyDeviceToHost);
+    if (v)
+        cudaMemset(t->perr, 0, 4);
+    return v;
 }
 
 // Most distinct prime factors of any y' <= y (primorials).
@@ -849,6 +1110,8 @@ int sieve_block_enqueue(const PrimeTable *t, const SieveLaunch &L, cudaStream_t 
                              kSieveWords * 4);
         cudaFuncSetAttribute(mu_sieve_byte_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kByteTile + kByteSqWords * 4);
+        cudaFuncSetAttribute(mu_sieve_persist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kByteTile + kByteSqWords * 4 + kMedMax * 4);
         attr_set = true;
     }
     const uint64_t y2 = L.y1 + L.len - 1;
@@ -865,7 +1128,7 @@ int sieve_block_enqueue(const PrimeTable *t, const SieveLaunch &L, cudaStream_t 
         ++launches;
     }
     if (bytes) {
-        ByteArgs b;
+        ByteArgs b{};
         b.y1 = L.y1;
         b.len = (uint32_t)L.len;
         b.np = np;
@@ -885,8 +1148,40 @@ int sieve_block_enqueue(const PrimeTable *t, const SieveLaunch &L, cudaStream_t 
         b.mu_base = L.mu_base;
         b.mu_end = L.mu_end;
         const uint32_t btiles = (uint32_t)((L.len + kByteTile - 1) / kByteTile);
-        mu_sieve_byte_kernel<<<btiles, kSieveThreads, kByteTile + kByteSqWords * 4, s>>>(b);
-        ++launches;
+        // the bucketed kernel pays once the primes above 2^17 outnumber the
+        // medium ones (2048 <= p < 2^17) more than 3:1 (measured crossover
+        // near y = 4e11); MERTENS_SIEVE_TILES / MERTENS_SIEVE_BUCKETS force
+        // one kernel (tests)
+        const uint32_t nmid = std::min(t->np_mid, np);
+        bool persist = np - nmid > 3u * (nmid - std::min(np_small, nmid));
+        if (getenv("MERTENS_SIEVE_BUCKETS"))
+            persist = true;
+        if (getenv("MERTENS_SIEVE_TILES"))
+            persist = false;
+        persist = persist && t->bucket && L.len <= t->scratch_len && np_small < np;
+        if (persist) {
+            int dev = 0, sms = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            // at least 64 CTAs keep a CTA's tiles within kPersistTilesMax
+            const uint32_t grid = std::min<uint32_t>((uint32_t)std::max(sms, 64), btiles);
+            b.np_mid = std::min(t->np_mid, np);
+            b.cap = t->bucket_cap;
+            b.pw = t->pw;
+            b.gsq = t->gsq;
+            b.bucket = t->bucket;
+            b.err = t->perr;
+            cudaMemsetAsync(t->gsq, 0, (size_t)btiles * (kByteTile / 8), s);
+            const uint32_t nsq = np - b.np_small;
+            square_bits_kernel<<<(nsq + 255) / 256, 256, 0, s>>>((uint32_t)L.len, b.np_small, np,
+                                                              t->p, t->blk_r2, t->gsq);
+            mu_sieve_persist_kernel<<<grid, kSieveThreads,
+                                      kByteTile + kByteSqWords * 4 + kMedMax * 4, s>>>(b);
+            launches += 2;
+        } else {
+            mu_sieve_byte_kernel<<<btiles, kSieveThreads, kByteTile + kByteSqWords * 4, s>>>(b);
+            ++launches;
+        }
     }
     const uint32_t tiles = bytes ? 0u : (uint32_t)((L.len + kSieveTile - 1) / kSieveTile);
     SieveArgs a;

@@ -100,7 +100,9 @@ int mertens_table_create(mertens_table_t *out, uint64_t y_max, mertens_u128 n_ma
         rc = MERTENS_ENOMEM;
     PrimeTable pt;
     if (rc == MERTENS_OK) {
-        const int prc = prime_table_create(&pt, t->al, y_max, s);
+        int prc = prime_table_create(&pt, t->al, y_max, s);
+        if (prc == 0)
+            prc = sieve_scratch_create(&pt, L);
         if (prc != 0)
             rc = prc == 2 ? MERTENS_ENOMEM : MERTENS_ECUDA;
     }
@@ -130,6 +132,10 @@ int mertens_table_create(mertens_table_t *out, uint64_t y_max, mertens_u128 n_ma
             rc = MERTENS_ECUDA;
         if (cudaStreamSynchronize(s) != cudaSuccess)
             rc = MERTENS_ECUDA;
+        if (rc == MERTENS_OK && sieve_scratch_status(&pt)) {
+            set_last_error("mertens_table_create: a sieve bucket overflowed its capacity");
+            rc = MERTENS_EOVERFLOW;
+        }
     }
     if (rc == MERTENS_ECUDA)
         set_last_error("mertens_table_create: %s", cudaGetErrorString(cudaGetLastError()));

@@ -87,20 +87,30 @@ def test_sieve_M_with_carry_far_from_one():
     assert np.array_equal(M.cpu().numpy().astype(np.int64), ref)
 
 
-@pytest.mark.parametrize("y1,length", [(1, 3 * 10**6 + 11), (7 * 10**9 + 1, 4 * BYTE_TILE + 999)])
-def test_byte_and_halfword_sieves_agree(y1, length, monkeypatch):
-    """The byte kernel and the 16-bit kernel give the same M(y), and both
-    match the oracle's mu."""
-    carry = 0 if y1 == 1 else oracle.mertens(y1 - 1, L=10**6)
-    M8 = torch.empty(length, dtype=torch.int32, device="cuda")
-    pm.mertens_sieve_M(y1, length, carry, M8)
-    monkeypatch.setenv("MERTENS_SIEVE16", "1")
-    M16 = torch.empty(length, dtype=torch.int32, device="cuda")
-    pm.mertens_sieve_M(y1, length, carry, M16)
-    a, b = M8.cpu().numpy(), M16.cpu().numpy()
-    assert np.array_equal(a, b)
+@pytest.mark.parametrize("y1,length", [
+    (1, 3 * 10**6 + 11),
+    (7 * 10**9 + 1, 4 * BYTE_TILE + 999),
+    (3 * 10**11 + 17, 300 * BYTE_TILE + 5),      # primes above 2^17: bucketed
+    (2**45 + 3, 70 * BYTE_TILE + 1),             # weight scale 3, 5.9e6 sieving primes
+])
+def test_sieve_kernels_agree(y1, length, monkeypatch):
+    """The persistent bucketed byte kernel, the per-tile byte kernel and the
+    16-bit kernel (each forced by its switch) give the same M(y), and match the
+    oracle's mu."""
+    # the carry only shifts every M(y); far out it is left at 0
+    carry = 0 if y1 == 1 or y1 > 10**12 else oracle.mertens(y1 - 1, L=10**7)
+    out = []
+    for env in ("MERTENS_SIEVE_BUCKETS", "MERTENS_SIEVE_TILES", "MERTENS_SIEVE16"):
+        if env:
+            monkeypatch.setenv(env, "1")
+        M = torch.empty(length, dtype=torch.int32, device="cuda")
+        pm.mertens_sieve_M(y1, length, carry, M)
+        out.append(M.cpu().numpy())
+        if env:
+            monkeypatch.delenv(env)
+    assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
     ref = carry + np.cumsum(oracle.mu_window(y1, length).astype(np.int64))
-    assert np.array_equal(a.astype(np.int64), ref)
+    assert np.array_equal(out[0].astype(np.int64), ref)
 
 
 def test_sieve_rejects_bad_arguments():
