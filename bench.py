@@ -42,6 +42,9 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--mode", choices=["auto", "replicas", "shard"], default="auto",
+                    help="N > 1: shard one target over the ranks by y-windows (auto, strong "
+                         "scaling) or run independent replicas (weak scaling)")
     ap.add_argument("--config", choices=sorted(CONFIGS), default="1e16")
     ap.add_argument("--no-cpu-baseline", action="store_true",
                     help="skip the timed oracle sample (cpu_baseline key)")
@@ -282,6 +285,97 @@ def serving_measure(sample: int):
             "over_one_per_plan": tab["queries_per_s"] / one["queries_per_s"],
         },
     }
+
+
+def run_sharded(args, world, rank, local):
+    """One target over `world` ranks: each rank runs its y-window (window
+    plan), the windows' carries and sums are exchanged (all-gather of mu sums,
+    all-reduce of the entries' sums), rank 0 resolves.  Strong scaling."""
+    import torch
+
+    import paper_1108_0135_gb300 as pm
+    from paper_1108_0135_gb300 import shard
+
+    cfg = CONFIGS[args.config]
+    pm.load()
+    pm.use_torch_allocator()
+    stream = torch.cuda.current_stream()
+    n, u, L = cfg["n"][0], cfg["u"], cfg["block_len"]
+    info = pm.mertens_describe(n, u)
+    terms = info["direct_terms"] + info["gathered_terms"]
+    device = torch.device("cuda", local) if world > 1 else None
+    tgt = shard.ShardedTarget(n, u, L, rank, world, device)
+    for _ in range(max(args.warmup, 1)):
+        arr = tgt.step(stream)
+    if rank == 0 and cfg["pin"] is not None and int(arr[0]) != cfg["pin"]:
+        raise SystemExit(f"wrong result: M({n}) = {int(arr[0])}, expected {cfg['pin']}")
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    t0 = time.perf_counter()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        arr = tgt.step(stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    wall_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    clk = clocks.stop()
+    # each step ends in host copies (the exchange, resolve), so the device
+    # interval between the events spans the whole step
+    ms = ev0.elapsed_time(ev1) / args.steps
+    ms_max = max_over_ranks(ms, world)
+    wall_max = max_over_ranks(wall_ms, world)
+    if rank == 0 and cfg["pin"] is not None:
+        assert int(arr[0]) == cfg["pin"]
+    # this rank's window, kernel by kernel with the library's phase events
+    phases = {}
+    if tgt.plan:
+        pm.mertens_plan_set_profiling(tgt.plan, True)
+        pm.mertens_run(tgt.plan, stream)
+        torch.cuda.synchronize()
+        st = pm.mertens_run_stats_get(tgt.plan)
+        phases = {"mu_sieve": st["sieve_ms"], "seg_carry": st["scan_ms"],
+                  "update_dense": st["dense_ms"], "update_gathered": st["gather_ms"]}
+        kernels = int(st["kernels"])
+        peaks, _ = load_peaks()
+        roofs = rooflines(phases, st, peaks, int(st["blocks"]), pm.mertens_probe_int_peaks(stream))
+    else:
+        kernels, roofs = 0, {}
+    window = tgt.window
+    tgt.close()
+    X = info["X"]
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": terms / (ms_max / 1e3), "unit": "update terms/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+            "dtype": "int64", "data": "synthetic",
+            "config": {"workload": cfg["workload"], "n": n, "u": u, "block_len": L,
+                       "X": info["X"], "terms_per_step": terms,
+                       "l2": "inputs larger than L2 (M blocks of 512 MiB)",
+                       "parallelism": f"y-windows over {world} ranks: window plans, all-gather "
+                                      f"of mu sums, all-reduce of entry sums, resolve on rank 0"},
+            "wall_time_s": ms_max / 1e3,
+            "host_wall_ms_per_step": wall_max,
+            "rank0_window": list(window),
+            "rank0_phases_ms": {k: round(v, 3) for k, v in phases.items()},
+            "clocks": clk,
+            # every step already reads the window sums to the host, exchanges
+            # them and resolves from host memory: its host wall time is the
+            # end-to-end figure
+            "e2e": {"value": terms / (wall_max / 1e3), "unit": "update terms/s",
+                    "h2d_bytes_per_step": 16 * X, "d2h_bytes_per_step": 16 * X,
+                    "ms_per_step": wall_max},
+            "gpu_launches": (kernels + 1) * args.steps,
+            "roofline": (roofs[max(roofs, key=lambda k: phases[k])] if roofs else None),
+            "rooflines_rank0": roofs,
+            "cpu_baseline": None,
+        }
+        print(json.dumps(line), flush=True)
 
 
 def run_native(args, world, rank, local):
@@ -556,7 +650,11 @@ def main():
         return
     world, rank, local = dist_init(args)
     try:
-        run_native(args, world, rank, local)
+        shard = args.mode == "shard" or (args.mode == "auto" and world > 1)
+        if shard:
+            run_sharded(args, world, rank, local)
+        else:
+            run_native(args, world, rank, local)
     finally:
         if world > 1:
             import torch.distributed as dist

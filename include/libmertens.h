@@ -150,6 +150,17 @@ int mertens_plan_window(mertens_plan_t *out, const mertens_u128 *n, size_t count
                         mertens_u128 u, uint64_t block_len, uint64_t y_first, uint64_t y_last);
 
 /*
+ * mertens_resolve -- the last step on its own (Sec. 2): given every entry's
+ * update sum S[x-1], x = 1..X = floor(n/u) (host array, uint64, mod 2^64 --
+ * for instance the windows of a partition of [1, y_max] added up as
+ * S_loc + C coef), computes M_out[x-1] = M(floor(n/x)) by
+ * M[x] = 1 - S[x] - sum_{j>=2} M[xj] on the device.  Host buffers; runs on
+ * `stream` and returns when done.  Errors: MERTENS_EINVAL, MERTENS_ENOMEM,
+ * MERTENS_ECUDA.
+ */
+int mertens_resolve(mertens_u128 n, uint64_t u, const uint64_t *S, int64_t *M_out, void *stream);
+
+/*
  * mertens_window_result -- wait for the last run of window plan `plan` and
  * return target i's partial sums: S_loc[x-1] and coef[x-1] for
  * x = 1..min(cap, X_i) (either may be NULL; uint64, mod 2^64), *len = X_i,

@@ -62,6 +62,7 @@ EXPORTS = [
     "mertens_server_destroy", "mertens_plan_window", "mertens_window_result",
     "mertens_table_create", "mertens_table_info", "mertens_plan_on_table", "mertens_table_destroy",
     "mertens_server_use_table", "mertens_scan_extremes", "mertens_probe_int_peaks",
+    "mertens_resolve",
 ]
 
 
@@ -135,6 +136,8 @@ def load():
         lib.mertens_server_use_table.restype = c_int
         lib.mertens_scan_extremes.argtypes = [u64, u64, i64, ctypes.POINTER(mertens_extremes), P]
         lib.mertens_scan_extremes.restype = c_int
+        lib.mertens_resolve.argtypes = [mertens_u128, u64, P, P, P]
+        lib.mertens_resolve.restype = c_int
         lib.mertens_probe_int_peaks.argtypes = [ctypes.POINTER(mertens_int_peaks), P]
         lib.mertens_probe_int_peaks.restype = c_int
         lib.mertens_table_destroy.argtypes = [P]
@@ -310,6 +313,17 @@ def mertens_scan_extremes(y_first: int, y_last: int, carry: int, stream=None) ->
     _check(load().mertens_scan_extremes(int(y_first), int(y_last), int(carry), ctypes.byref(e),
                                         _stream(stream)), "mertens_scan_extremes")
     return {name: getattr(e, name) for name, _ in mertens_extremes._fields_}
+
+
+def mertens_resolve(n: int, u: int, S, stream=None) -> np.ndarray:
+    """M(floor(n/x)), x = 1..X, from the entries' update sums S (uint64, X = n//u)."""
+    S = np.ascontiguousarray(S, dtype=np.uint64)
+    out = np.zeros(S.size, dtype=np.int64)
+    if S.size != int(n) // int(u):
+        raise ValueError("S must have floor(n/u) entries")
+    _check(load().mertens_resolve(u128(n), int(u), S.ctypes.data, out.ctypes.data,
+                                  _stream(stream)), "mertens_resolve")
+    return out
 
 
 def mertens_probe_int_peaks(stream=None) -> dict:

@@ -1504,6 +1504,51 @@ int mertens_result(mertens_plan_t p, size_t i, int64_t *M_n, int64_t *entries, s
     return MERTENS_OK;
 }
 
+int mertens_resolve(mertens_u128 n, uint64_t u, const uint64_t *S, int64_t *M_out, void *stream)
+{
+    if (check_n(n, "mertens_resolve", 0) != MERTENS_OK || !S || !M_out)
+        return MERTENS_EINVAL;
+    const u128 nn = to_u128(n);
+    if (check_u(nn, u) != MERTENS_OK || nn / u >= ((u128)1 << 32)) {
+        set_last_error("mertens_resolve: need floor(sqrt(n)) < u <= n and n/u < 2^32");
+        return MERTENS_EINVAL;
+    }
+    const uint64_t X = (uint64_t)(nn / u);
+    cudaStream_t s = (cudaStream_t)stream;
+    const Allocator al = current_allocator();
+    std::vector<uint64_t> K(X);
+    for (uint64_t x = 1; x <= X; ++x) {
+        const u128 k = nn / x;
+        K[x - 1] = k >= kTwo63 ? 0 : (uint64_t)k;  // only k == 1 is looked at
+    }
+    uint64_t *dS = (uint64_t *)dev_alloc(al, X * 8);
+    uint64_t *dK = (uint64_t *)dev_alloc(al, X * 8);
+    uint64_t *dR = (uint64_t *)dev_alloc(al, X * 8);
+    QueryDev *dq = (QueryDev *)dev_alloc(al, sizeof(QueryDev));
+    int rc = MERTENS_OK;
+    if (!dS || !dK || !dR || !dq)
+        rc = MERTENS_ENOMEM;
+    if (rc == MERTENS_OK) {
+        QueryDev q;
+        q.X = X;
+        q.off = 0;
+        if (cudaMemcpyAsync(dS, S, X * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(dK, K.data(), X * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(dq, &q, sizeof q, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            resolve_enqueue(dq, 1, dS, dK, dR, s) < 0 ||
+            cudaMemcpyAsync(M_out, dR, X * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            rc = MERTENS_ECUDA;
+    }
+    if (rc == MERTENS_ECUDA)
+        set_last_error("mertens_resolve: %s", cudaGetErrorString(cudaGetLastError()));
+    dev_free(al, dS, X * 8);
+    dev_free(al, dK, X * 8);
+    dev_free(al, dR, X * 8);
+    dev_free(al, dq, sizeof(QueryDev));
+    return rc;
+}
+
 int mertens_plan_on_table(mertens_plan_t *out, mertens_table_t table, const mertens_u128 *n,
                           size_t count, mertens_u128 u, uint64_t block_len)
 {

@@ -390,6 +390,21 @@ def test_windows_partition_equals_whole_run(wide_from, monkeypatch):
     assert np.array_equal(got, oracle.mertens_array(n, n // u, L=10**8))
 
 
+def test_sharded_target_one_rank_equals_whole_run():
+    """shard.ShardedTarget with one rank: the window [1, y_max] through a
+    window plan, then mertens_resolve on its sums, equals a whole run."""
+    from paper_1108_0135_gb300 import shard
+    n, u = 10**12 + 12345, 10**8
+    m, arr = gpu_array(n, u, 2**22)
+    t = shard.ShardedTarget(n, u, 2**22)
+    try:
+        got = t.step()
+        got2 = t.step()
+    finally:
+        t.close()
+    assert np.array_equal(got, arr) and np.array_equal(got2, arr)
+
+
 def test_window_two_word_target_at_1e13():
     """n = 10^20 with u ~ n^(2/3): four 2^22-y blocks from y = 10^13, against
     carry-free sums from the oracle's mu window (entries x <= 10 are two-word)."""
