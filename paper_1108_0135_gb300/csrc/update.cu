@@ -301,7 +301,8 @@ __global__ void __launch_bounds__(256) sparse_update_kernel(SparseBlockArgs b, S
 // sum_j M(floor(k/j)) = sum_j (staged value) + count * M(t1-1).  Warps take
 // 32 entries at a time (lane per entry for the range), then each entry with
 // terms in turn, lanes over its j.
-__global__ void __launch_bounds__(512) gather_tile_kernel(GatherArgs a)
+// Three 512-thread CTAs per SM (64 KiB of tile each): registers capped to fit.
+__global__ void __launch_bounds__(512, 3) gather_tile_kernel(GatherArgs a)
 {
     extern __shared__ int16_t Mt[];  // kGatherTile
     __shared__ uint32_t s_item;
