@@ -726,18 +726,24 @@ __global__ void __launch_bounds__(kSieveThreads, 1) mu_sieve_persist_kernel(Byte
             if (job < js) {
                 byte_small_job(s_jd[job], w, sq, lane);
             } else if (job < jm) {
-                // 64 medium primes, two per lane, offsets carried in shared memory
-#pragma unroll
-                for (uint32_t h = 0; h < 2; ++h) {
-                    const uint32_t i = (job - js) * 64u + h * 32u + lane;
-                    if (i < nmed) {
-                        const uint32_t pwv = a.pw[a.np_small + i];
-                        const uint32_t p = pwv & 0xffffffu, wt = pwv >> 24;
-                        uint32_t yo = moff[i];
-                        for (; yo < tl; yo += p)
-                            atomicAdd(&w[yo >> 2], __funnelshift_l(0u, wt, yo << 3));
-                        moff[i] = yo - (uint32_t)kByteTile;
-                    }
+                // 64 medium primes, two per lane, both loads issued first;
+                // offsets carried in shared memory
+                const uint32_t i0 = (job - js) * 64u + lane, i1 = i0 + 32u;
+                const uint32_t pw0 = i0 < nmed ? a.pw[a.np_small + i0] : 0u;
+                const uint32_t pw1 = i1 < nmed ? a.pw[a.np_small + i1] : 0u;
+                uint32_t o0 = i0 < nmed ? moff[i0] : 0xffffffffu;
+                uint32_t o1 = i1 < nmed ? moff[i1] : 0xffffffffu;
+                if (i0 < nmed) {
+                    const uint32_t p = pw0 & 0xffffffu, wt = pw0 >> 24;
+                    for (; o0 < tl; o0 += p)
+                        atomicAdd(&w[o0 >> 2], __funnelshift_l(0u, wt, o0 << 3));
+                    moff[i0] = o0 - (uint32_t)kByteTile;
+                }
+                if (i1 < nmed) {
+                    const uint32_t p = pw1 & 0xffffffu, wt = pw1 >> 24;
+                    for (; o1 < tl; o1 += p)
+                        atomicAdd(&w[o1 >> 2], __funnelshift_l(0u, wt, o1 << 3));
+                    moff[i1] = o1 - (uint32_t)kByteTile;
                 }
             } else {
                 // bucket entries of this tile: mark, forward to the tile of the
