@@ -595,7 +595,7 @@ def window_measure(stream):
 TRAFFIC_PER_LAUNCH = {
     "mu_sieve": 1.058e6 + 476.671e6,       # profiles/mu_sieve_byte_1e16.md (one 2^28-y block)
     "update_dense": 989.370e6 + 5.861e6,   # profiles/dense_update_1e16.md
-    "update_gathered": None,                # kernel changed since the last capture
+    "update_gathered": 1539.031e6 + 19.648e6,  # profiles/gather_tile_1e16.md (first block)
 }
 
 SIX_OVER_PI2 = 6.0 / math.pi ** 2

@@ -554,6 +554,16 @@ def test_plans_on_table_match_oracle(table_2e26, n, block_len):
     assert m == m2 and np.array_equal(arr, arr2)
 
 
+def test_two_word_entries_on_table(table_2e26, monkeypatch):
+    """Entries forced through the two-word kernel read M(y) from the table."""
+    n = 10**12 + 12345
+    (m, arr), = _run_on_table(table_2e26, [n])
+    monkeypatch.setenv("MERTENS_WIDE_FROM", str(10**9))
+    (m2, arr2), = _run_on_table(table_2e26, [n])
+    assert m2 == m and np.array_equal(arr2, arr)
+    assert m == oracle.mertens(n, L=10**8)
+
+
 def test_batch_on_table_same_as_alone(table_2e26):
     ns = [10**12 + 7, 3 * 10**11, 5 * 10**7, 10**13, 123_456_789_012]
     batch = _run_on_table(table_2e26, ns)
