@@ -512,6 +512,11 @@ def run_native(args, world, rank, local):
                                          "divisor table 1.3 GB per step)",
                        "parallelism": f"{world} independent replicas"},
             "wall_time_s": ms_max / 1e3,
+            # `value` counts the paper's direct + gathered terms (closed form per
+            # entry); the kernels reach the same sums through the mu-form, which
+            # executes one quotient per squarefree y below the dense cut-off and
+            # one per gathered j above it:
+            "terms_executed_per_step": SIX_OVER_PI2 * stats["dense_y"] + stats["gather_j"],
             "phases_ms": {k: round(v, 3) for k, v in phases.items()},
             "y_sieved_per_s": stats["y_sieved"] * world / (ms_max / 1e3),
             "clocks": clk,
