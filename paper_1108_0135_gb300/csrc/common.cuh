@@ -121,6 +121,69 @@ __device__ __forceinline__ uint32_t div_magic32(uint32_t v, uint32_t m, unsigned
     return __umulhi(v, m) >> s;
 }
 
+// ---------------------------------------------------------------------------
+// Bulk asynchronous copies global -> shared (cp.async.bulk, completing on an
+// mbarrier in shared memory) with bounded waits.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kErrTimeout = 8u;       // a bounded wait gave up
+constexpr uint32_t kBulkWaitLimit = 1u << 20;  // tries of at most ~1 us each
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// One arrival expected (the thread that issues the copies).
+__device__ __forceinline__ void mbar_init(uint64_t *mbar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar)) : "memory");
+}
+
+// Orders this thread's earlier shared-memory accesses (and an mbarrier init)
+// before later asynchronous-proxy accesses.
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// The issuing thread's arrival, announcing `bytes` to come (< 2^20).
+__device__ __forceinline__ void mbar_arrive_expect(uint64_t *mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// dst (shared) <- src (global), `bytes` a multiple of 16, both 16-byte aligned.
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes,
+                                              uint64_t *mbar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(mbar))
+        : "memory");
+}
+
+// Waits (bounded) for phase `parity` of the mbarrier to complete; false when
+// the limit was reached first.
+__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity)
+{
+    for (uint32_t it = 0; it < kBulkWaitLimit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 1000;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(smem_addr(mbar)), "r"(parity)
+            : "memory");
+        if (done)
+            return true;
+    }
+    return false;
+}
+
 // Warp-wide sum of a 64-bit value (mod 2^64).
 __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v)
 {

@@ -218,9 +218,12 @@ int mertens_scan_extremes(uint64_t y_first, uint64_t y_last, int64_t carry,
              cudaMemcpyAsync(&last, cy + nblocks, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
              cudaStreamSynchronize(s) != cudaSuccess))
             rc = MERTENS_ECUDA;
-        if (rc == MERTENS_OK && sieve_scratch_status(&pt)) {
-            set_last_error("mertens_scan_extremes: a sieve bucket overflowed its capacity");
-            rc = MERTENS_EOVERFLOW;
+        if (rc == MERTENS_OK) {
+            const uint32_t st = sieve_scratch_status(&pt);
+            if (st) {
+                set_last_error("mertens_scan_extremes: %s", sieve_status_text(st));
+                rc = sieve_status_code(st);
+            }
         }
         if (rc == MERTENS_OK) {
             out->M_last = last;

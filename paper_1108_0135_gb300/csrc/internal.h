@@ -82,6 +82,17 @@ int sieve_scratch_create(PrimeTable *t, uint64_t max_len);
 // Status bits the persistent sieve left since the last call (and clears them):
 // kErrBucket when a bucket overflowed (the block's M(y) is then wrong).
 uint32_t sieve_scratch_status(PrimeTable *t);
+// The status code and the text for those bits: a bounded wait that gave up
+// (MERTENS_ETIMEOUT) or an overflowed bucket (MERTENS_EOVERFLOW).
+inline int sieve_status_code(uint32_t st)
+{
+    return (st & kErrTimeout) ? MERTENS_ETIMEOUT : MERTENS_EOVERFLOW;
+}
+inline const char *sieve_status_text(uint32_t st)
+{
+    return (st & kErrTimeout) ? "a bounded wait for a bulk copy in the sieve gave up"
+                              : "a sieve bucket overflowed its capacity";
+}
 // Number of primes in the table that are <= b.
 uint32_t prime_count_upto(const PrimeTable *t, uint64_t b);
 // Enqueues the fused steps a1 + a2 for one block.  Returns the number of

@@ -1483,9 +1483,12 @@ int mertens_result(mertens_plan_t p, size_t i, int64_t *M_n, int64_t *entries, s
         set_last_error("mertens_result: |M(y)| exceeded the int32 block type");
         return MERTENS_EOVERFLOW;
     }
-    if (!p->table && sieve_scratch_status(&p->pt)) {
-        set_last_error("mertens_result: a sieve bucket overflowed its capacity");
-        return MERTENS_EOVERFLOW;
+    if (!p->table) {
+        const uint32_t st = sieve_scratch_status(&p->pt);
+        if (st) {
+            set_last_error("mertens_result: %s", sieve_status_text(st));
+            return sieve_status_code(st);
+        }
     }
     if (len)
         *len = p->X[i];
@@ -1595,9 +1598,12 @@ int mertens_window_result(mertens_plan_t p, size_t i, uint64_t *S_loc, uint64_t 
         set_last_error("mertens_window_result: %s", cudaGetErrorString(cudaGetLastError()));
         return MERTENS_ECUDA;
     }
-    if (!p->table && sieve_scratch_status(&p->pt)) {
-        set_last_error("mertens_window_result: a sieve bucket overflowed its capacity");
-        return MERTENS_EOVERFLOW;
+    if (!p->table) {
+        const uint32_t st = sieve_scratch_status(&p->pt);
+        if (st) {
+            set_last_error("mertens_window_result: %s", sieve_status_text(st));
+            return sieve_status_code(st);
+        }
     }
     if (len)
         *len = p->X[i];
@@ -1776,9 +1782,12 @@ static int sieve_window(uint64_t y1, uint64_t len, int8_t *mu_dev, int64_t carry
             rc = MERTENS_ECUDA;
         if (rc == MERTENS_OK && (e & kErrMOverflow))
             rc = MERTENS_EOVERFLOW;
-        if (rc == MERTENS_OK && sieve_scratch_status(&pt)) {
-            set_last_error("sieve: a sieve bucket overflowed its capacity");
-            rc = MERTENS_EOVERFLOW;
+        if (rc == MERTENS_OK) {
+            const uint32_t st = sieve_scratch_status(&pt);
+            if (st) {
+                set_last_error("sieve: %s", sieve_status_text(st));
+                rc = sieve_status_code(st);
+            }
         }
     }
     if (rc == MERTENS_ECUDA)

@@ -534,6 +534,7 @@ __global__ void __launch_bounds__(kSieveThreads, 1) mu_sieve_byte_kernel(ByteArg
     uint32_t *sq = w + kByteWords;                     // kByteSqWords words, 32 y each
     __shared__ uint32_t s_job;
     __shared__ uint4 s_jd[kByteJobsMax];
+    __shared__ uint64_t s_mbar;
     const uint32_t a0 = blockIdx.x * (uint32_t)kByteTile;
     const uint64_t t1 = a.y1 + a0;
     const uint32_t tl = min(a.len - a0, (uint32_t)kByteTile);
@@ -546,20 +547,32 @@ __global__ void __launch_bounds__(kSieveThreads, 1) mu_sieve_byte_kernel(ByteArg
     // pre-sieve pattern (bytes of 2, 3, 5, 7, square flags of 4, 9, 25, 49)
     uint32_t single = kNone;
     {
+        // the tile's bytes: one bulk asynchronous copy of the pattern phase,
+        // overlapped with the job descriptors and the square flags
+        const uint32_t ph = (uint32_t)(t1 % kPatternPeriod);
+        if (threadIdx.x == 0) {
+            mbar_init(&s_mbar);
+            fence_proxy_async_smem();
+            mbar_arrive_expect(&s_mbar, (uint32_t)kByteTile);
+            bulk_copy_g2s(sb, a.pat8 + (size_t)(ph & 15u) * (kPat8Len / 16) + (ph >> 4),
+                          (uint32_t)kByteTile, &s_mbar);
+            s_job = 0;
+        }
         if (threadIdx.x < js)
             s_jd[threadIdx.x] = byte_small_desc(a, threadIdx.x, jp, a0, tl, &single);
-        const uint32_t ph = (uint32_t)(t1 % kPatternPeriod);
-        const uint4 *src = a.pat8 + (size_t)(ph & 15u) * (kPat8Len / 16) + (ph >> 4);
-#pragma unroll 4
-        for (uint32_t i = threadIdx.x; i < (uint32_t)kByteTile / 16; i += kSieveThreads)
-            sb[i] = src[i];
         const uint32_t j0 = ph >> 5, s = ph & 31u;
         for (uint32_t i = threadIdx.x; i < (uint32_t)kByteSqWords; i += kSieveThreads)
             sq[i] = __funnelshift_r(a.patsq[j0 + i], a.patsq[j0 + i + 1], s);
-        if (threadIdx.x == 0)
-            s_job = 0;
     }
-    __syncthreads();
+    __syncthreads();  // the mbarrier is initialised
+    if (__syncthreads_or(!mbar_wait(&s_mbar, 0u))) {
+        // the copy did not land in time: flag it, give it one more bounded
+        // wait (it writes this CTA's shared memory), and leave the tile
+        if (threadIdx.x == 0 && a.err)
+            atomicOr(a.err, kErrTimeout);
+        mbar_wait(&s_mbar, 0u);
+        return;
+    }
     if (single != kNone)
         atomicOr(&sq[single >> 5], 1u << (single & 31u));
 
@@ -650,6 +663,7 @@ __global__ void __launch_bounds__(kSieveThreads, 1) mu_sieve_persist_kernel(Byte
     __shared__ uint32_t s_job;
     __shared__ uint4 s_jd[kByteJobsMax];
     __shared__ uint32_t s_cnt[kPersistTilesMax];
+    __shared__ uint64_t s_mbar;
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     const uint32_t ntiles = (a.len + kByteTile - 1) / kByteTile;
     const uint32_t tb = (uint32_t)((uint64_t)blockIdx.x * ntiles / gridDim.x);
@@ -663,6 +677,10 @@ __global__ void __launch_bounds__(kSieveThreads, 1) mu_sieve_persist_kernel(Byte
     // CTA prologue: next multiple of every medium prime, buckets of the large
     for (uint32_t i = threadIdx.x; i < kPersistTilesMax; i += kSieveThreads)
         s_cnt[i] = 0;
+    if (threadIdx.x == 0) {
+        mbar_init(&s_mbar);
+        fence_proxy_async_smem();
+    }
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < nmed; i += kSieveThreads) {
         const uint32_t t = a.np_small + i;
@@ -699,21 +717,30 @@ __global__ void __launch_bounds__(kSieveThreads, 1) mu_sieve_persist_kernel(Byte
         const uint32_t jobs = jm + (nb + kBucketJob - 1) / kBucketJob;
         uint32_t single = kNone;
         {
+            // bulk copy of the tile's pattern bytes (the previous tile's
+            // readers are past the barrier that ended it), overlapped with
+            // the descriptors and the square flags
+            const uint32_t ph = (uint32_t)(t1 % kPatternPeriod);
+            if (threadIdx.x == 0) {
+                fence_proxy_async_smem();
+                mbar_arrive_expect(&s_mbar, (uint32_t)kByteTile);
+                bulk_copy_g2s(sb, a.pat8 + (size_t)(ph & 15u) * (kPat8Len / 16) + (ph >> 4),
+                              (uint32_t)kByteTile, &s_mbar);
+                s_job = 0;
+            }
             if (threadIdx.x < js)
                 s_jd[threadIdx.x] = byte_small_desc(a, threadIdx.x, jp, a0, tl, &single);
-            const uint32_t ph = (uint32_t)(t1 % kPatternPeriod);
-            const uint4 *src = a.pat8 + (size_t)(ph & 15u) * (kPat8Len / 16) + (ph >> 4);
-#pragma unroll 4
-            for (uint32_t i = threadIdx.x; i < (uint32_t)kByteTile / 16; i += kSieveThreads)
-                sb[i] = src[i];
             const uint32_t j0 = ph >> 5, sh = ph & 31u;
             const uint32_t *gs = a.gsq + (a0 >> 5);
             for (uint32_t i = threadIdx.x; i < (uint32_t)kByteSqWords; i += kSieveThreads)
                 sq[i] = __funnelshift_r(a.patsq[j0 + i], a.patsq[j0 + i + 1], sh) | gs[i];
-            if (threadIdx.x == 0)
-                s_job = 0;
         }
-        __syncthreads();
+        if (__syncthreads_or(!mbar_wait(&s_mbar, tt & 1u))) {
+            if (threadIdx.x == 0)
+                atomicOr(a.err, kErrTimeout);
+            mbar_wait(&s_mbar, tt & 1u);
+            return;
+        }
         if (single != kNone)
             atomicOr(&sq[single >> 5], 1u << (single & 31u));
         for (;;) {
@@ -1153,6 +1180,7 @@ int sieve_block_enqueue(const PrimeTable *t, const SieveLaunch &L, cudaStream_t 
         b.mu_out = L.mu_out;
         b.mu_base = L.mu_base;
         b.mu_end = L.mu_end;
+        b.err = t->perr;  // bounded-wait status (null without scratch)
         const uint32_t btiles = (uint32_t)((L.len + kByteTile - 1) / kByteTile);
         // the bucketed kernel pays once the primes above 2^17 outnumber the
         // medium ones (2048 <= p < 2^17) more than 3:1 (measured crossover

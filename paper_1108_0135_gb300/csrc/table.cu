@@ -132,9 +132,12 @@ int mertens_table_create(mertens_table_t *out, uint64_t y_max, mertens_u128 n_ma
             rc = MERTENS_ECUDA;
         if (cudaStreamSynchronize(s) != cudaSuccess)
             rc = MERTENS_ECUDA;
-        if (rc == MERTENS_OK && sieve_scratch_status(&pt)) {
-            set_last_error("mertens_table_create: a sieve bucket overflowed its capacity");
-            rc = MERTENS_EOVERFLOW;
+        if (rc == MERTENS_OK) {
+            const uint32_t st = sieve_scratch_status(&pt);
+            if (st) {
+                set_last_error("mertens_table_create: %s", sieve_status_text(st));
+                rc = sieve_status_code(st);
+            }
         }
     }
     if (rc == MERTENS_ECUDA)
