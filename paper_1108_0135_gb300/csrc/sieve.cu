@@ -320,6 +320,7 @@ struct ByteArgs {
     int32_t *segsum;
     int8_t *mu_out;
     uint64_t mu_base, mu_end;
+    uint32_t extra_tx;    // bytes announced beyond the copy (0; tests of the bounded wait)
     // persistent kernel only
     const uint32_t *pw;   // p | w(p) << 24 for p < 2^17
     const uint32_t *gsq;  // square flags of primes >= 2048 over the block (one bit per y)
@@ -553,7 +554,7 @@ __global__ void __launch_bounds__(kSieveThreads, 1) mu_sieve_byte_kernel(ByteArg
         if (threadIdx.x == 0) {
             mbar_init(&s_mbar);
             fence_proxy_async_smem();
-            mbar_arrive_expect(&s_mbar, (uint32_t)kByteTile);
+            mbar_arrive_expect(&s_mbar, (uint32_t)kByteTile + a.extra_tx);
             bulk_copy_g2s(sb, a.pat8 + (size_t)(ph & 15u) * (kPat8Len / 16) + (ph >> 4),
                           (uint32_t)kByteTile, &s_mbar);
             s_job = 0;
@@ -723,7 +724,7 @@ __global__ void __launch_bounds__(kSieveThreads, 1) mu_sieve_persist_kernel(Byte
             const uint32_t ph = (uint32_t)(t1 % kPatternPeriod);
             if (threadIdx.x == 0) {
                 fence_proxy_async_smem();
-                mbar_arrive_expect(&s_mbar, (uint32_t)kByteTile);
+                mbar_arrive_expect(&s_mbar, (uint32_t)kByteTile + a.extra_tx);
                 bulk_copy_g2s(sb, a.pat8 + (size_t)(ph & 15u) * (kPat8Len / 16) + (ph >> 4),
                               (uint32_t)kByteTile, &s_mbar);
                 s_job = 0;
@@ -1181,6 +1182,9 @@ int sieve_block_enqueue(const PrimeTable *t, const SieveLaunch &L, cudaStream_t 
         b.mu_base = L.mu_base;
         b.mu_end = L.mu_end;
         b.err = t->perr;  // bounded-wait status (null without scratch)
+        // MERTENS_TEST_STALL_COPY: announce 16 bytes that never come, so the
+        // bounded wait runs out (the test of that error path)
+        b.extra_tx = (getenv("MERTENS_TEST_STALL_COPY") && t->perr) ? 16u : 0u;
         const uint32_t btiles = (uint32_t)((L.len + kByteTile - 1) / kByteTile);
         // the bucketed kernel pays once the primes above 2^17 outnumber the
         // medium ones (2048 <= p < 2^17) more than 3:1 (measured crossover

@@ -113,6 +113,23 @@ def test_sieve_kernels_agree(y1, length, monkeypatch):
     assert np.array_equal(out[0].astype(np.int64), ref)
 
 
+def test_bounded_copy_wait_reports_timeout_and_device_stays_usable(monkeypatch):
+    """The sieve's bulk-copy wait is bounded: with MERTENS_TEST_STALL_COPY the
+    barrier is told to expect 16 bytes that never arrive, the wait gives up
+    (about a second), the call reports MERTENS_ETIMEOUT, and the next call on
+    the same device is correct."""
+    y1, length = 2**30 + 1, BYTE_TILE + 100
+    M = torch.empty(length, dtype=torch.int32, device="cuda")
+    monkeypatch.setenv("MERTENS_TEST_STALL_COPY", "1")
+    with pytest.raises(pm.MertensError) as ei:
+        pm.mertens_sieve_M(y1, length, 0, M)
+    assert ei.value.code == pm._lib.MERTENS_ETIMEOUT
+    monkeypatch.delenv("MERTENS_TEST_STALL_COPY")
+    pm.mertens_sieve_M(y1, length, 0, M)
+    ref = np.cumsum(oracle.mu_window(y1, length).astype(np.int64))
+    assert np.array_equal(M.cpu().numpy().astype(np.int64), ref)
+
+
 def test_sieve_rejects_bad_arguments():
     mu = torch.empty(64, dtype=torch.int8, device="cuda")
     with pytest.raises(pm.MertensError):
