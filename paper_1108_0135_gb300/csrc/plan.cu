@@ -937,7 +937,7 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
         const int nbuf = p->serial ? 1 : 2;
         for (int i = 0; i < 2; ++i) {
             if (i < nbuf) {
-                p->dMloc[i] = p->alloc<int16_t>(L + 2);
+                p->dMloc[i] = p->alloc<int16_t>(L + 16);  // tiles copy whole 16-byte units
                 p->dsegsum[i] = p->alloc<int32_t>(nseg);
                 p->dsegoff[i] = p->alloc<int64_t>(nseg);
             } else {
@@ -1315,6 +1315,7 @@ static int run_enqueue(mertens_plan_s *p, cudaStream_t origin, uint64_t *out)
                 ga.counter = p->dcounter_gather;
                 ga.Mloc = Mb;
                 ga.segoff = Sb;
+                ga.err = p->derr;
                 ga.threads = serial ? 512 : 256;
                 ga.ctas_per_sm = serial ? 0 : 2;
                 ga.K = p->dK;
@@ -1479,16 +1480,20 @@ int mertens_result(mertens_plan_t p, size_t i, int64_t *M_n, int64_t *entries, s
     uint32_t err = 0;
     if (cudaMemcpy(&err, p->derr, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
         return MERTENS_ECUDA;
-    if (err & kErrMOverflow) {
-        set_last_error("mertens_result: |M(y)| exceeded the int32 block type");
-        return MERTENS_EOVERFLOW;
-    }
     if (!p->table) {
         const uint32_t st = sieve_scratch_status(&p->pt);
         if (st) {
             set_last_error("mertens_result: %s", sieve_status_text(st));
             return sieve_status_code(st);
         }
+    }
+    if (err & kErrTimeout) {
+        set_last_error("mertens_result: a bounded wait for a bulk copy in the update gave up");
+        return MERTENS_ETIMEOUT;
+    }
+    if (err & kErrMOverflow) {
+        set_last_error("mertens_result: |M(y)| exceeded the int32 block type");
+        return MERTENS_EOVERFLOW;
     }
     if (len)
         *len = p->X[i];
@@ -1780,8 +1785,8 @@ static int sieve_window(uint64_t y1, uint64_t len, int8_t *mu_dev, int64_t carry
         if (cudaMemcpyAsync(&e, er, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess)
             rc = MERTENS_ECUDA;
-        if (rc == MERTENS_OK && (e & kErrMOverflow))
-            rc = MERTENS_EOVERFLOW;
+        // the sieve's own status first: a tile it gave up on leaves garbage
+        // that the int32 check below would report instead
         if (rc == MERTENS_OK) {
             const uint32_t st = sieve_scratch_status(&pt);
             if (st) {
@@ -1789,6 +1794,8 @@ static int sieve_window(uint64_t y1, uint64_t len, int8_t *mu_dev, int64_t carry
                 rc = sieve_status_code(st);
             }
         }
+        if (rc == MERTENS_OK && (e & kErrMOverflow))
+            rc = MERTENS_EOVERFLOW;
     }
     if (rc == MERTENS_ECUDA)
         set_last_error("sieve: %s", cudaGetErrorString(cudaGetLastError()));

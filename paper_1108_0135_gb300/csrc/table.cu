@@ -82,7 +82,7 @@ int mertens_table_create(mertens_table_t *out, uint64_t y_max, mertens_u128 n_ma
 
     const uint64_t nseg = sieve_segments(y_max);
     const uint64_t nchunks = dense_chunks(t->ydense);
-    t->Mloc = table_alloc<int16_t>(t, y_max + 2);
+    t->Mloc = table_alloc<int16_t>(t, y_max + 16);  // gather tiles copy whole 16-byte units
     t->segoff = table_alloc<int64_t>(t, nseg);
     t->MG = table_alloc<uint64_t>(t, t->mg_n + 1);
     t->dl_m = table_alloc<uint64_t>(t, nchunks * kChunkCapPad);

@@ -307,8 +307,14 @@ __global__ void __launch_bounds__(512, 3) gather_tile_kernel(GatherArgs a)
     extern __shared__ int16_t Mt[];  // kGatherTile
     __shared__ uint32_t s_item;
     __shared__ int64_t s_base;
+    __shared__ int32_t s_delta[kGatherTile / kSegY];
+    __shared__ uint64_t s_mbar;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    uint32_t staged = 0xffffffffu;
+    uint32_t staged = 0xffffffffu, phase = 0;
+    if (threadIdx.x == 0) {
+        mbar_init(&s_mbar);
+        fence_proxy_async_smem();
+    }
     for (;;) {
         if (threadIdx.x == 0)
             s_item = atomicAdd(a.counter, 1u);
@@ -319,12 +325,37 @@ __global__ void __launch_bounds__(512, 3) gather_tile_kernel(GatherArgs a)
         const GatherItem I = a.items[it];
         const GatherTile T = a.tiles[I.tile];
         if (I.tile != staged) {
-            const uint64_t o1 = T.t1 - a.y1;
-            const int64_t base = (o1 == 0) ? a.segoff[0] : block_M(a.segoff, a.Mloc, o1 - 1);
-            for (uint32_t i = threadIdx.x; i < T.len; i += blockDim.x)
-                Mt[i] = (int16_t)(block_M(a.segoff, a.Mloc, o1 + i) - base);
-            if (threadIdx.x == 0)
-                s_base = base;
+            // stage M(y) - M(t1 - 1) of the tile: one bulk asynchronous copy
+            // of the block's int16 values (whole 16-byte units; the buffer is
+            // padded), then each 2048-y segment's offset added in place
+            const uint64_t o1 = T.t1 - a.y1;  // a multiple of the tile length
+            const uint32_t n8 = (T.len + 7u) & ~7u;
+            if (threadIdx.x == 0) {
+                fence_proxy_async_smem();  // earlier readers of Mt passed the barrier
+                mbar_arrive_expect(&s_mbar, n8 * 2u);
+                bulk_copy_g2s(Mt, a.Mloc + o1, n8 * 2u, &s_mbar);
+                s_base = (o1 == 0) ? a.segoff[0] : block_M(a.segoff, a.Mloc, o1 - 1);
+            }
+            __syncthreads();
+            const uint32_t nseg = (T.len + kSegY - 1) / kSegY;
+            if (threadIdx.x < nseg)
+                s_delta[threadIdx.x] =
+                    (int32_t)(a.segoff[(o1 >> kSegShift) + threadIdx.x] - s_base);
+            if (__syncthreads_or(!mbar_wait(&s_mbar, phase & 1u))) {
+                if (threadIdx.x == 0)
+                    atomicOr(a.err, kErrTimeout);
+                mbar_wait(&s_mbar, phase & 1u);
+                return;
+            }
+            ++phase;
+            uint32_t *Mw = reinterpret_cast<uint32_t *>(Mt);
+            for (uint32_t i = threadIdx.x; i < n8 / 2u; i += blockDim.x) {
+                const uint32_t v = Mw[i];
+                const int32_t d = s_delta[(2u * i) >> kSegShift];
+                const uint32_t lo = (uint32_t)((int32_t)(int16_t)(v & 0xffffu) + d) & 0xffffu;
+                const uint32_t hi = (uint32_t)((int32_t)(int16_t)(v >> 16) + d);
+                Mw[i] = lo | (hi << 16);
+            }
             staged = I.tile;
         }
         __syncthreads();

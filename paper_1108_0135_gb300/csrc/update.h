@@ -95,6 +95,7 @@ struct GatherArgs {
     uint64_t *S;
     uint32_t threads;      // 256 or 512 per CTA
     uint32_t ctas_per_sm;  // 0: as many as fit; else at most this many per SM
+    uint32_t *err;         // status word: kErrTimeout when a bounded wait gave up
 };
 
 // Array entry with k = floor(n/x) >= 2^63 (targets n >= 2^63 only): its k
