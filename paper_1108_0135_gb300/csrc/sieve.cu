@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -891,23 +892,25 @@ static uint32_t byte_weight(uint32_t p, uint32_t S)
     return 2u * (uint32_t)std::floor((x - 1.0) / 2.0 + 0.5) + 1u;
 }
 
-// Tables of the byte sieve (see mu_sieve_byte_kernel).
-static int byte_tables_create(PrimeTable *t, const std::vector<uint32_t> &pr, cudaStream_t s)
+// Host copies of the byte sieve's pre-sieve tables for weight scale S (they
+// depend on S only): built once per process and kept.
+struct BytePatterns {
+    std::vector<uint8_t> p8;     // 16 phase copies of the 2, 3, 5, 7 byte pattern
+    std::vector<uint32_t> psq;   // square flags of 4, 9, 25, 49 as a bit string
+};
+
+static const BytePatterns &byte_patterns(uint32_t S)
 {
-    const size_t np = pr.size();
-    std::vector<uint4> pq(np);
-    for (size_t i = 0; i < np; ++i) {
-        const uint32_t p = pr[i];
-        unsigned s1 = 0, s2 = 0;
-        const uint32_t m1 = magic32_of(p, &s1);
-        const uint64_t p2 = (uint64_t)p * p;
-        const uint32_t m2 = p2 < (1ull << 30) ? magic32_of((uint32_t)p2, &s2) : 0u;
-        pq[i] = make_uint4(p, m1, m2, s1 | (s2 << 8) | (byte_weight(p, t->byte_scale) << 16));
-    }
+    static std::mutex mu;
+    static BytePatterns cache[5];
+    std::lock_guard<std::mutex> lk(mu);
+    BytePatterns &bp = cache[S < 5 ? S : 4];
+    if (!bp.p8.empty())
+        return bp;
     uint32_t w[4];
     const uint32_t small[4] = {2, 3, 5, 7};
     for (int q = 0; q < 4; ++q)
-        w[q] = byte_weight(small[q], t->byte_scale);
+        w[q] = byte_weight(small[q], S);
     std::vector<uint8_t> pat(kPatternPeriod);
     std::vector<uint8_t> sqp(kPatternPeriod);
     for (uint32_t i = 0; i < kPatternPeriod; ++i) {
@@ -921,14 +924,33 @@ static int byte_tables_create(PrimeTable *t, const std::vector<uint32_t> &pr, cu
         pat[i] = (uint8_t)b;
         sqp[i] = (uint8_t)f;
     }
-    std::vector<uint8_t> p8((size_t)16 * kPat8Len);
+    bp.p8.resize((size_t)16 * kPat8Len);
     for (uint32_t k = 0; k < 16; ++k)
         for (uint32_t j = 0; j < kPat8Len; ++j)
-            p8[(size_t)k * kPat8Len + j] = pat[(k + j) % kPatternPeriod];
-    std::vector<uint32_t> psq(kPatSqWords, 0u);
+            bp.p8[(size_t)k * kPat8Len + j] = pat[(k + j) % kPatternPeriod];
+    bp.psq.assign(kPatSqWords, 0u);
     for (uint32_t j = 0; j < 32u * kPatSqWords; ++j)
         if (sqp[j % kPatternPeriod])
-            psq[j >> 5] |= 1u << (j & 31u);
+            bp.psq[j >> 5] |= 1u << (j & 31u);
+    return bp;
+}
+
+// Tables of the byte sieve (see mu_sieve_byte_kernel).
+static int byte_tables_create(PrimeTable *t, const std::vector<uint32_t> &pr, cudaStream_t s)
+{
+    const size_t np = pr.size();
+    std::vector<uint4> pq(np);
+    for (size_t i = 0; i < np; ++i) {
+        const uint32_t p = pr[i];
+        unsigned s1 = 0, s2 = 0;
+        const uint32_t m1 = magic32_of(p, &s1);
+        const uint64_t p2 = (uint64_t)p * p;
+        const uint32_t m2 = p2 < (1ull << 30) ? magic32_of((uint32_t)p2, &s2) : 0u;
+        pq[i] = make_uint4(p, m1, m2, s1 | (s2 << 8) | (byte_weight(p, t->byte_scale) << 16));
+    }
+    const BytePatterns &bp = byte_patterns(t->byte_scale);
+    const std::vector<uint8_t> &p8 = bp.p8;
+    const std::vector<uint32_t> &psq = bp.psq;
     // p | w << 24 for the primes below 2^17
     uint32_t nmid = 0;
     while (nmid < np && pr[nmid] < (1u << 17))
