@@ -598,9 +598,9 @@ def window_measure(stream):
 # DRAM bytes (read + write) per launch from one ncu capture of the current
 # kernel (profiles/), or None when the kernel changed since the capture.
 TRAFFIC_PER_LAUNCH = {
-    "mu_sieve": 1.058e6 + 476.671e6,       # profiles/mu_sieve_byte_1e16.md (one 2^28-y block)
+    "mu_sieve": 1.053e6 + 476.298e6,       # profiles/mu_sieve_byte_1e16.md (one 2^28-y block)
     "update_dense": 989.370e6 + 5.861e6,   # profiles/dense_update_1e16.md
-    "update_gathered": 1539.031e6 + 19.648e6,  # profiles/gather_tile_1e16.md (first block)
+    "update_gathered": 509.817e6 + 4.147e6,  # profiles/gather_tile_1e16.md (first block)
 }
 
 SIX_OVER_PI2 = 6.0 / math.pi ** 2
@@ -612,24 +612,28 @@ def rooflines(phases, stats, peaks, nblocks, ipk):
     Every class here is bound by integer issue (no tensor cores, no floating
     point; HBM traffic is ~2 B per sieved y).  Denominators are measured on
     this device by mertens_probe_int_peaks (ipk):
-      update_dense, update_gathered: the update's inner step acc +=
-        mulhi64(m, 2k) >> l, in terms/s (the 64x64 multiply-high runs on the
-        FMA-heavy pipe; ncu shows that pipe as the limiter of both kernels).
-        Algorithmic terms: squarefree y of the dense ranges ((6/pi^2) x the
-        summed dense y-range) and one per gathered j.
+      update_dense: the update's inner step acc += mulhi64(m, 2k) >> l, in
+        terms/s (the 64x64 multiply-high runs on the FMA-heavy pipe; ncu
+        shows that pipe as the kernel's limiter).  Algorithmic terms:
+        squarefree y of the dense ranges ((6/pi^2) x the summed dense y-range).
+      update_gathered: one term per gathered j, against the faster of that
+        step and the shared-memory gather's float-estimate quotient step
+        (the tile kernel takes the latter, the global path the former).
       mu_sieve: 32-bit ALU lane operations/s (LOP3 + IADD3 chains).
         Algorithmic operations: one per sieve update (y, p | y or p^2 | y
         for every sieving prime p) plus two per y (decision + scan add)."""
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     mulhi_peak = ipk["mulhi_terms_per_s"] / 1e12
     alu_peak = 2.0 * ipk["alu_pairs_per_s"] / 1e12
+    gather_peak = max(ipk["mulhi_terms_per_s"], ipk.get("fquot_terms_per_s", 0.0)) / 1e12
     work = {
         "mu_sieve": (stats["sieve_updates"] + 2.0 * stats["y_sieved"], alu_peak, "T int-op/s",
                      "measured: LOP3+IADD3 chains on all SMs, 2 ops per pair"),
         "update_dense": (SIX_OVER_PI2 * stats["dense_y"], mulhi_peak, "T mulhi-terms/s",
                          "measured: acc += mulhi64(m,2k) >> l chains on all SMs"),
-        "update_gathered": (float(stats["gather_j"]), mulhi_peak, "T mulhi-terms/s",
-                            "measured: acc += mulhi64(m,2k) >> l chains on all SMs"),
+        "update_gathered": (float(stats["gather_j"]), gather_peak, "T terms/s",
+                            "measured: the faster of the mulhi64 step and the float-estimate "
+                            "quotient step, chains on all SMs"),
     }
     launches = {"mu_sieve": nblocks, "update_dense": 1, "update_gathered": nblocks}
     out = {}

@@ -347,17 +347,19 @@ int mertens_scan_extremes(uint64_t y_first, uint64_t y_last, int64_t carry,
 /*
  * mertens_probe_int_peaks -- measured integer rates of the current device,
  * for roofline denominators (no counterpart in the paper): the update's
- * inner step acc += mulhi64(m, 2k) >> l (terms/s), 32-bit IMAD (per s) and
- * LOP3+IADD3 pairs (per s), each from the best of two timed runs of
- * independent chains over the whole device after one warm-up run.  Runs on
- * `stream`, returns when done.  Errors: MERTENS_EINVAL, MERTENS_ENOMEM,
- * MERTENS_ECUDA.
+ * inner step acc += mulhi64(m, 2k) >> l (terms/s), 32-bit IMAD (per s),
+ * LOP3+IADD3 pairs (per s) and the shared-memory gather's quotient step
+ * (float estimate of (k - t1 j)/j, truncation, one exact remainder test;
+ * terms/s), each from the best of two timed runs of independent chains over
+ * the whole device after one warm-up run.  Runs on `stream`, returns when
+ * done.  Errors: MERTENS_EINVAL, MERTENS_ENOMEM, MERTENS_ECUDA.
  */
 typedef struct {
     double mulhi_terms_per_s;
     double imad32_per_s;
     double alu_pairs_per_s;
     int sms;
+    double fquot_terms_per_s;
 } mertens_int_peaks;
 int mertens_probe_int_peaks(mertens_int_peaks *out, void *stream);
 

@@ -76,7 +76,8 @@ class mertens_extremes(ctypes.Structure):
 
 class mertens_int_peaks(ctypes.Structure):
     _fields_ = [("mulhi_terms_per_s", ctypes.c_double), ("imad32_per_s", ctypes.c_double),
-                ("alu_pairs_per_s", ctypes.c_double), ("sms", ctypes.c_int)]
+                ("alu_pairs_per_s", ctypes.c_double), ("sms", ctypes.c_int),
+                ("fquot_terms_per_s", ctypes.c_double)]
 
 
 class mertens_tuning(ctypes.Structure):

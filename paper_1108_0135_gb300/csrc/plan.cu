@@ -171,6 +171,7 @@ struct mertens_plan_s {
     std::vector<uint64_t> direct, gathered, ymax_q;
     uint64_t nent = 0;
     uint64_t y_max = 0, block_len = 0, nblocks = 0, ydense = 0, jmax = 0, mg_n = 0;
+    uint32_t gquot = 1;  // GatherArgs::quot of this plan
     // sieved range: [1, y_max] for a whole run; a window plan runs only the
     // blocks of [y_first, y_last], with M(y_first - 1) taken as 0, and returns
     // per entry S_loc and the coefficient of that carry (coef)
@@ -708,6 +709,16 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
                 p->jmax = std::max(p->jmax, std::min(JC0[e], K[e] / p->y_first));
     }
     p->mg_n = std::max(p->jmax, p->ydense) + 1;
+    // quotients of the shared-memory gather: the float estimate, with a
+    // 32-bit remainder while every gathered j is below 2^31 (MERTENS_GATHER_QUOT
+    // = 0 forces the multiply-high magics, = 2 the 64-bit remainder)
+    p->gquot = p->jmax < (1ull << 31) ? 1u : 2u;
+    if (const char *e = getenv("MERTENS_GATHER_QUOT")) {
+        if (e[0] == '0')
+            p->gquot = 0;
+        else if (e[0] == '2')
+            p->gquot = 2;
+    }
     if (table && (p->y_max > table->y_max || p->ydense > table->ydense ||
                   p->mg_n > table->mg_n)) {
         set_last_error("mertens_plan_on_table: the targets need y, dense cut-offs or divisors "
@@ -1318,6 +1329,7 @@ static int run_enqueue(mertens_plan_s *p, cudaStream_t origin, uint64_t *out)
                 ga.err = p->derr;
                 ga.threads = serial ? 512 : 256;
                 ga.ctas_per_sm = serial ? 0 : 2;
+                ga.quot = p->gquot;
                 ga.K = p->dK;
                 ga.JLO = p->dJLO;
                 ga.JCUR = p->dJCUR;

@@ -6,7 +6,8 @@
 // The update's quotient q = floor(k/d) = mulhi64(m_d, 2k) >> l_d is one
 // 64x64 -> 128-bit multiply-high, a shift and an add per term; the probe runs
 // exactly that step in eight independent accumulators per thread, with the
-// multiplier changing every step so nothing can be hoisted.
+// multiplier changing every step so nothing can be hoisted; a fourth probe
+// runs the shared-memory gather's float-estimate quotient the same way.
 #include <cstdint>
 
 #include "../../include/libmertens.h"
@@ -38,6 +39,49 @@ __global__ void __launch_bounds__(kProbeThreads) probe_mulhi_kernel(uint64_t *ou
 #pragma unroll
     for (int j = 0; j < kProbeChains; ++j)
         s ^= acc[j];
+    out[tid] = s;
+}
+
+// The gathered terms' float-estimate quotient (the shared-memory gather's
+// step): R and j stepped by fused multiply-adds, f = R (1/j) rounded to an
+// integer through the 1.5 2^23 bias, one exact 32-bit remainder test.
+__global__ void __launch_bounds__(kProbeThreads) probe_fquot_kernel(uint64_t *out, uint32_t t1,
+                                                                   int iters)
+{
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t R[kProbeChains], j[kProbeChains], acc[kProbeChains];
+    float Rf0[kProbeChains], jf0[kProbeChains];
+#pragma unroll
+    for (int c = 0; c < kProbeChains; ++c) {
+        R[c] = (uint32_t)(tid * 977ull) + (uint32_t)c * 131u;
+        j[c] = 100000000u + (uint32_t)(tid & 1023u) * 32u + (uint32_t)c;
+        Rf0[c] = (float)R[c];
+        jf0[c] = (float)j[c];
+        acc[c] = 0;
+    }
+    const uint32_t dR = t1 << 5;
+    const float dRf = (float)dR;
+    float fi = 0.0f;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < kProbeChains; ++c) {
+            const float Rf = __fmaf_rn(fi, dRf, Rf0[c]), jf = __fmaf_rn(fi, -32.0f, jf0[c]);
+            float rj;
+            asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rj) : "f"(jf));
+            const float t = __fadd_rn(__fmaf_rn(Rf, rj, -0.53125f), 12582912.0f);
+            uint32_t q = (uint32_t)(__float_as_int(t) - 0x4B400000);
+            const uint32_t rem = R[c] - q * j[c];
+            q += rem >= j[c] ? 1u : 0u;
+            acc[c] += q;
+            R[c] += dR;
+            j[c] -= 32u;
+        }
+        fi += 1.0f;
+    }
+    uint64_t s = 0;
+#pragma unroll
+    for (int c = 0; c < kProbeChains; ++c)
+        s ^= acc[c];
     out[tid] = s;
 }
 
@@ -105,9 +149,9 @@ extern "C" int mertens_probe_int_peaks(mertens_int_peaks *out, void *stream)
         return MERTENS_ENOMEM;
     }
     const double ops = (double)nthr * iters * kProbeChains;
-    double rate[3] = {0, 0, 0};
+    double rate[4] = {0, 0, 0, 0};
     int rc = MERTENS_OK;
-    for (int which = 0; which < 3 && rc == MERTENS_OK; ++which) {
+    for (int which = 0; which < 4 && rc == MERTENS_OK; ++which) {
         float best = 0;
         for (int rep = 0; rep < 3; ++rep) {  // the first run warms up
             cudaEventRecord(a, s);
@@ -115,8 +159,10 @@ extern "C" int mertens_probe_int_peaks(mertens_int_peaks *out, void *stream)
                 probe_mulhi_kernel<<<blocks, kProbeThreads, 0, s>>>(buf, 0xF00DBABEDEADBEEFull, iters);
             else if (which == 1)
                 probe_imad_kernel<<<blocks, kProbeThreads, 0, s>>>(buf, 2654435761u, iters);
-            else
+            else if (which == 2)
                 probe_alu_kernel<<<blocks, kProbeThreads, 0, s>>>(buf, 2654435761u, iters);
+            else
+                probe_fquot_kernel<<<blocks, kProbeThreads, 0, s>>>(buf, 1000007u, iters);
             cudaEventRecord(b, s);
             float ms = 0;
             if (cudaEventSynchronize(b) != cudaSuccess ||
@@ -141,5 +187,6 @@ extern "C" int mertens_probe_int_peaks(mertens_int_peaks *out, void *stream)
     out->imad32_per_s = rate[1];
     out->alu_pairs_per_s = rate[2];
     out->sms = sms;
+    out->fquot_terms_per_s = rate[3];
     return MERTENS_OK;
 }

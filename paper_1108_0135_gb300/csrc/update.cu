@@ -293,6 +293,56 @@ __global__ void __launch_bounds__(256) sparse_update_kernel(SparseBlockArgs b, S
     }
 }
 
+// Quotient of a gathered term inside a tile.  With R = k - t1 j, the term's
+// y - t1 = floor(R / j) and 0 <= R < len j, len <= 2^15, so the quotient Q is
+// below 2^15.  The float path estimates it without any conversion unit (on
+// this part the 64-bit integer -> float conversion runs on the FP64 pipe):
+// R and j come from float_of (exact 16- and 23-bit pieces, two roundings:
+// relative error <= 2^-23) at the start of a lane's run and are then stepped
+// with one fused multiply-add each from the run's start (R_i = R_0 + i dR,
+// j_i = j_0 + i dj, one rounding each, so the error stays within 2^-22 of the
+// current value, or, where R falls, within 2^-22 R_0); 1/j is rcp.approx
+// (<= 1 ulp).  So R (1/j) is within 1/40 of Q (relative errors near 2^-21 on
+// values below 2^15), and rounding R (1/j) - 17/32 to an integer (adding
+// 1.5 2^23 makes the float addition round to an integer, read back from the
+// bits) gives floor(Q) or floor(Q) - 1; the exact remainder R - q j, in
+// [0, 2j), decides the step.  kQuotF32 takes the remainder in 32 bits (every
+// j < 2^31, so 2j < 2^32), kQuotF64 in 64.  The result is clamped to
+// lim = len - 1, which keeps the shared-memory index inside the tile whatever
+// the estimate.  kQuotMagic keeps the 64-bit multiply-high path.
+constexpr int kQuotMagic = 0, kQuotF32 = 1, kQuotF64 = 2;
+static_assert(kGatherTile <= 32768, "the quotient bound needs tiles of at most 2^15 y");
+
+// v (< 2^55) as a float with relative error at most 2^-23, from exact pieces:
+// a 23-bit integer p is the float with bits 0x4B000000 | p, less 2^23.
+__device__ __forceinline__ float float_of(uint64_t v)
+{
+    const uint32_t lo = (uint32_t)v, hi = (uint32_t)(v >> 32);
+    const float fh = __int_as_float(0x4B000000 | hi) - 8388608.0f;
+    const float fa = __int_as_float(0x4B000000 | (lo >> 16)) - 8388608.0f;
+    const float fb = __int_as_float(0x4B000000 | (lo & 0xffffu)) - 8388608.0f;
+    return __fmaf_rn(fh, 4294967296.0f, __fmaf_rn(fa, 65536.0f, fb));
+}
+
+template <int kQuot>
+__device__ __forceinline__ uint32_t tile_quot(float Rf, float jf, uint64_t R, uint32_t j,
+                                              uint32_t lim)
+{
+    float rj;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rj) : "f"(jf));
+    const float t = __fadd_rn(__fmaf_rn(Rf, rj, -0.53125f), 12582912.0f);
+    const int32_t qs = __float_as_int(t) - 0x4B400000;  // floor(Q) or floor(Q) - 1 (>= -1)
+    uint32_t q = (uint32_t)qs;
+    if (kQuot == kQuotF32) {
+        const uint32_t rem = (uint32_t)R - q * j;
+        q += rem >= j ? 1u : 0u;
+    } else {
+        const uint64_t rem = R - (uint64_t)((int64_t)qs * (int64_t)j);
+        q += rem >= j ? 1u : 0u;
+    }
+    return q < lim ? q : lim;
+}
+
 // Shared-memory gather path for the low, dense part of a block.  A work item
 // is one tile [t1, t1+len) of y and a range of entries of one target.  The
 // tile's M(y) - M(t1-1) is staged in shared memory as int16 (|value| <= 3/4
@@ -302,6 +352,8 @@ __global__ void __launch_bounds__(256) sparse_update_kernel(SparseBlockArgs b, S
 // 32 entries at a time (lane per entry for the range), then each entry with
 // terms in turn, lanes over its j.
 // Three 512-thread CTAs per SM (64 KiB of tile each): registers capped to fit.
+// kQuot picks how a term's quotient is taken (tile_quot above).
+template <int kQuot>
 __global__ void __launch_bounds__(512, 3) gather_tile_kernel(GatherArgs a)
 {
     extern __shared__ int16_t Mt[];  // kGatherTile
@@ -374,15 +426,26 @@ __global__ void __launch_bounds__(512, 3) gather_tile_kernel(GatherArgs a)
             // j < 2^32 (j <= sqrt(k) < 2^32) and y - t1 < 2^15: 32-bit loop
             // counters and offsets
             const uint32_t cnt = jt >= jb ? (uint32_t)(jt - jb + 1) : 0u;
-            const uint32_t t1lo = (uint32_t)T.t1;
+            const uint32_t t1lo = (uint32_t)T.t1, lim = T.len - 1u;
             // entries with few terms: one lane each, serially
             if (cnt > 0 && cnt <= kLaneTerms) {
                 int acc = 0;
                 const uint32_t j0 = (uint32_t)jb;
-                for (uint32_t i = 0; i < cnt; ++i) {
-                    const uint32_t j = j0 + i;
-                    const uint64_t y = div_magic(k2, a.MG[j], 32u - __clz(j - 1u));
-                    acc += Mt[(uint32_t)y - t1lo];
+                if (kQuot == kQuotMagic) {
+                    for (uint32_t i = 0; i < cnt; ++i) {
+                        const uint32_t j = j0 + i;
+                        const uint64_t y = div_magic(k2, a.MG[j], 32u - __clz(j - 1u));
+                        acc += Mt[(uint32_t)y - t1lo];
+                    }
+                } else {
+                    // R = k - t1 j falls by t1 per step of j
+                    uint64_t R = (k2 >> 1) - T.t1 * (uint64_t)j0;
+                    const float Rf0 = float_of(R), jf0 = float_of(j0), t1f = float_of(T.t1);
+                    float fi = 0.0f;
+                    for (uint32_t i = 0; i < cnt; ++i, R -= T.t1, fi += 1.0f) {
+                        const float Rf = __fmaf_rn(fi, -t1f, Rf0), jf = __fadd_rn(jf0, fi);
+                        acc += Mt[tile_quot<kQuot>(Rf, jf, R, j0 + i, lim)];
+                    }
                 }
                 const int64_t tot = (int64_t)acc + (int64_t)cnt * base;
                 atomicAdd(reinterpret_cast<unsigned long long *>(a.S + e), (unsigned long long)tot);
@@ -397,13 +460,28 @@ __global__ void __launch_bounds__(512, 3) gather_tile_kernel(GatherArgs a)
                 const uint64_t k2s = __shfl_sync(0xffffffffu, k2, src);
                 int acc = 0;
                 if ((uint32_t)lane < cns) {
-                    // lanes over j descending, 32 apart; the magic pointer is
-                    // walked rather than indexed (measured faster)
+                    // lanes over j descending, 32 apart
                     uint32_t j = jts - (uint32_t)lane;
-                    const uint64_t *mp = a.MG + j;
-                    for (uint32_t i = (uint32_t)lane; i < cns; i += 32u, j -= 32u, mp -= 32) {
-                        const uint64_t y = div_magic(k2s, *mp, 32u - __clz(j - 1u));
-                        acc += Mt[(uint32_t)y - t1lo];
+                    if (kQuot == kQuotMagic) {
+                        // the magic pointer is walked rather than indexed
+                        // (measured faster)
+                        const uint64_t *mp = a.MG + j;
+                        for (uint32_t i = (uint32_t)lane; i < cns; i += 32u, j -= 32u, mp -= 32) {
+                            const uint64_t y = div_magic(k2s, *mp, 32u - __clz(j - 1u));
+                            acc += Mt[(uint32_t)y - t1lo];
+                        }
+                    } else {
+                        // R = k - t1 j rises by 32 t1 per step, j falls by 32
+                        uint64_t R = (k2s >> 1) - T.t1 * (uint64_t)j;
+                        const uint64_t dR = T.t1 << 5;
+                        const float Rf0 = float_of(R), jf0 = float_of(j), dRf = float_of(dR);
+                        float fi = 0.0f;
+                        for (uint32_t i = (uint32_t)lane; i < cns;
+                             i += 32u, j -= 32u, R += dR, fi += 1.0f) {
+                            const float Rf = __fmaf_rn(fi, dRf, Rf0);
+                            const float jf = __fmaf_rn(fi, -32.0f, jf0);
+                            acc += Mt[tile_quot<kQuot>(Rf, jf, R, j, lim)];
+                        }
                     }
                 }
                 int64_t tot = warp_sum_i64((int64_t)acc);
@@ -669,16 +747,24 @@ int gather_tiles_enqueue(const GatherArgs &a, cudaStream_t s)
     static bool attr = false;
     const int smem = kGatherTile * 2;
     if (!attr) {
-        cudaFuncSetAttribute(gather_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(gather_tile_kernel<kQuotMagic>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(gather_tile_kernel<kQuotF32>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(gather_tile_kernel<kQuotF64>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         attr = true;
     }
     if (a.nitems == 0)
         return 0;
+    void (*kern)(GatherArgs) = a.quot == kQuotF32   ? gather_tile_kernel<kQuotF32>
+                               : a.quot == kQuotF64 ? gather_tile_kernel<kQuotF64>
+                                                    : gather_tile_kernel<kQuotMagic>;
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int threads = a.threads == 256 ? 256 : 512;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, gather_tile_kernel, threads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, smem);
     if (per < 1)
         per = 1;
     if (a.ctas_per_sm && (int)a.ctas_per_sm < per)
@@ -687,7 +773,7 @@ int gather_tiles_enqueue(const GatherArgs &a, cudaStream_t s)
     if (grid > a.nitems)
         grid = a.nitems;
     cudaMemsetAsync(a.counter, 0, 4, s);
-    gather_tile_kernel<<<grid, threads, smem, s>>>(a);
+    kern<<<grid, threads, smem, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 

@@ -96,6 +96,8 @@ struct GatherArgs {
     uint32_t threads;      // 256 or 512 per CTA
     uint32_t ctas_per_sm;  // 0: as many as fit; else at most this many per SM
     uint32_t *err;         // status word: kErrTimeout when a bounded wait gave up
+    uint32_t quot;         // 0: multiply-high magics; 1: float estimate, 32-bit
+                           // remainder (every j < 2^31); 2: float, 64-bit
 };
 
 // Array entry with k = floor(n/x) >= 2^63 (targets n >= 2^63 only): its k

@@ -5,6 +5,7 @@ Small cases compare whole arrays; the full-size n = 10^16 configuration is
 checked against Table 1 of the paper and on sampled entries the oracle
 computes one by one.
 """
+import functools
 import math
 import os
 
@@ -210,6 +211,27 @@ def test_dense_cutoff_does_not_change_results():
             os.environ.pop("MERTENS_DENSE_C", None)
         else:
             os.environ["MERTENS_DENSE_C"] = old
+
+
+@functools.lru_cache(maxsize=None)
+def _oracle_array(n, X):
+    return oracle.mertens_array(n, X, L=10**7)
+
+
+@pytest.mark.parametrize("mode", ["0", "2", None])
+@pytest.mark.parametrize("n,u,bl", [(10**11 + 7, 3 * 10**7, 1 << 22),
+                                    (10**12 + 39, 10**8, 1 << 24)])
+def test_gather_quotient_paths(n, u, bl, mode, monkeypatch):
+    """The shared-memory gather takes a term's quotient floor(k/j) by the
+    multiply-high magics (0), by a float estimate with a 64-bit remainder (2)
+    or, by default here, with a 32-bit one: all give the oracle's array."""
+    if mode is None:
+        monkeypatch.delenv("MERTENS_GATHER_QUOT", raising=False)
+    else:
+        monkeypatch.setenv("MERTENS_GATHER_QUOT", mode)
+    ref = _oracle_array(n, n // u)
+    _, arr = gpu_array(n, u, bl)
+    assert np.array_equal(arr, ref)
 
 
 def test_batch_same_alone_and_in_mix():
