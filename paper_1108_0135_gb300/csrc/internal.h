@@ -1,6 +1,7 @@
 // Host-side declarations shared by the libmertens translation units.
 #pragma once
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 #include <utility>
@@ -100,6 +101,24 @@ uint32_t prime_count_upto(const PrimeTable *t, uint64_t b);
 int sieve_block_enqueue(const PrimeTable *t, const SieveLaunch &L, cudaStream_t s);
 // Segments of a block of `len` y values.
 inline uint64_t sieve_segments(uint64_t len) { return (len + kSegY - 1) / kSegY; }
+
+// A kernel's attributes belong to each device's copy of it: the launch sites
+// that raise a dynamic shared-memory limit keep one bit per device in an
+// atomic word, set after the attributes (a race only repeats the setting).
+inline uint64_t device_bit()
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return 1ull << (dev & 63);
+}
+inline bool attrs_needed(const std::atomic<uint64_t> &done, uint64_t bit)
+{
+    return (done.load(std::memory_order_acquire) & bit) == 0;
+}
+inline void attrs_done(std::atomic<uint64_t> &done, uint64_t bit)
+{
+    done.fetch_or(bit, std::memory_order_release);
+}
 // M(y) of a window as int32 (the step-level entry point); sets *err bit 1 on
 // an int32 overflow.
 int expand_M_enqueue(const int16_t *Mloc, const int64_t *segoff, uint64_t len, int32_t *M,

@@ -1160,15 +1160,16 @@ static bool byte_path_ok(const PrimeTable *t, uint64_t y2, uint64_t P, uint64_t 
 
 int sieve_block_enqueue(const PrimeTable *t, const SieveLaunch &L, cudaStream_t s)
 {
-    static bool attr_set = false;
-    if (!attr_set) {
+    static std::atomic<uint64_t> attr_devs{0};
+    const uint64_t dbit = device_bit();
+    if (attrs_needed(attr_devs, dbit)) {
         cudaFuncSetAttribute(mu_sieve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kSieveWords * 4);
         cudaFuncSetAttribute(mu_sieve_byte_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kByteTile + kByteSqWords * 4);
         cudaFuncSetAttribute(mu_sieve_persist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kByteTile + kByteSqWords * 4 + kMedMax * 4);
-        attr_set = true;
+        attrs_done(attr_devs, dbit);
     }
     const uint64_t y2 = L.y1 + L.len - 1;
     uint64_t P = isqrt_u64(y2);

@@ -617,12 +617,13 @@ int dense_list_enqueue(const int8_t *mu_aux, uint64_t ydense, const uint64_t *MG
 
 int dense_update_enqueue(const DenseArgs &a, cudaStream_t s)
 {
-    static bool attr = false;
+    static std::atomic<uint64_t> attr_devs{0};
     const size_t smem = (size_t)kDenseChunks * kChunkCapPad * (8 + 2);
-    if (!attr) {
+    const uint64_t dbit = device_bit();
+    if (attrs_needed(attr_devs, dbit)) {
         cudaFuncSetAttribute(dense_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
-        attr = true;
+        attrs_done(attr_devs, dbit);
     }
     if (a.nitems == 0)
         return 0;
@@ -744,16 +745,17 @@ int wide_update_enqueue(const WideArgs &a, uint32_t nw, uint32_t grid_x, cudaStr
 
 int gather_tiles_enqueue(const GatherArgs &a, cudaStream_t s)
 {
-    static bool attr = false;
+    static std::atomic<uint64_t> attr_devs{0};
     const int smem = kGatherTile * 2;
-    if (!attr) {
+    const uint64_t dbit = device_bit();
+    if (attrs_needed(attr_devs, dbit)) {
         cudaFuncSetAttribute(gather_tile_kernel<kQuotMagic>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         cudaFuncSetAttribute(gather_tile_kernel<kQuotF32>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         cudaFuncSetAttribute(gather_tile_kernel<kQuotF64>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        attr = true;
+        attrs_done(attr_devs, dbit);
     }
     if (a.nitems == 0)
         return 0;
