@@ -92,6 +92,23 @@ def test_two_ranks_exchange_and_resolve(n, u, tmp_path):
     assert np.array_equal(got, oracle.mertens_array(n, n // u, L=10**5))
 
 
+def test_work_model_matches_measured_step():
+    """The work density integrates to about the measured n = 10^16 step (0.19 s
+    on one GB300), so sieve and update work are weighed in the same unit."""
+    from paper_1108_0135_gb300 import _lib as L
+    from paper_1108_0135_gb300 import shard
+
+    n, u = 10**16, 4 * 10**10
+    info = L.mertens_describe(n, u)
+    ys = np.unique(np.concatenate([np.geomspace(1.0, float(info["y_max"]), 8192),
+                                   np.linspace(1.0, float(info["y_max"]), 8192)]))
+    w = shard.work_density(ys, n, info["X"])
+    total = float(np.sum(0.5 * (w[1:] + w[:-1]) * np.diff(ys)))
+    assert 0.12 < total < 0.3
+    sieve = shard.SIEVE_S_PER_Y * info["y_max"]
+    assert 0.2 < sieve / total < 0.5          # the sieve is about a third of the step
+
+
 def test_window_bounds_partition():
     from paper_1108_0135_gb300 import _lib as L
     from paper_1108_0135_gb300 import shard
