@@ -67,8 +67,7 @@ int mertens_set_allocator(mertens_alloc_fn alloc, mertens_free_fn release, void 
 
 /*
  * mertens_plan -- prepare the computation of M(n_i), i < count, with one
- * shared sieve pass (Sec. 2: "if we want to compute M(x) for multiple close
- * values of x, we only need to do sieving once").
+ * shared sieve pass (Sec. 2 notes that close targets can share one sieve).
  *
  *   out        receives the plan (owned by the caller; free with
  *              mertens_destroy).
@@ -87,8 +86,8 @@ int mertens_set_allocator(mertens_alloc_fn alloc, mertens_free_fn release, void 
  *              allowed for n_i = 1), else MERTENS_EINVAL.  u < 2^64 (else
  *              MERTENS_ENOTSUP).  Each target's array has X_i = floor(n_i/u_i)
  *              entries (Sec. 2); X_i >= 2^32 is MERTENS_ENOTSUP.
- *   block_len  length of a sieve block in y (Sec. 3, "divide calculations
- *              into blocks of y"); 0 = chosen by the library.  Any value >= 1
+ *   block_len  length of a sieve block in y (Sec. 3 processes the y-axis
+ *              block by block); 0 = chosen by the library.  Any value >= 1
  *              is honoured exactly.
  *
  * Allocates all device memory of the plan on the current device (through the
@@ -175,8 +174,9 @@ int mertens_window_result(mertens_plan_t plan, size_t i, uint64_t *S_loc, uint64
  * mertens_run -- enqueue the whole computation on `stream`: for every sieve
  * block, mu_sieve (segmented Moebius sieve, Sec. 3), m_scan (M(y) by prefix
  * sum with the carry of the previous block), mertens_update (every array
- * entry's contributions from the block, Sec. 2-3); then resolve (Sec. 2, "it
- * is a simple task to compute final values of M").  Returns once everything
+ * entry's contributions from the block, Sec. 2-3); then resolve (Sec. 2: the
+ * final values of M follow from the update sums by the recursion).  Returns
+ * once everything
  * is enqueued; the work runs asynchronously.  May be called again on the same
  * plan (the arrays are reset first).  Errors: MERTENS_EINVAL (NULL plan),
  * MERTENS_ECUDA (a launch failed).
@@ -188,8 +188,8 @@ int mertens_run(mertens_plan_t plan, void *stream);
  * target i's results.
  *   M_n      receives M(n_i) (may be NULL).
  *   entries  NULL, or a host buffer of `cap` int64 that receives
- *            M(floor(n_i/x)) for x = 1..min(cap, X_i) -- the paper's array,
- *            "all values of M(y) for y = floor(n/c)" (Sec. 1-2).
+ *            M(floor(n_i/x)) for x = 1..min(cap, X_i) -- the paper's array
+ *            of M at every floor(n/x) (Sec. 1-2).
  *   len      receives X_i (may be NULL).
  * Values are exact; they are computed mod 2^64 and read as int64, which is
  * exact while |M| < 2^63.  Errors: MERTENS_EINVAL (bad i), MERTENS_ENOTREADY
@@ -275,8 +275,8 @@ int mertens_sieve_mu(uint64_t y1, uint64_t len, int8_t *mu_dev, void *stream);
 
 /*
  * mertens_sieve_M -- steps a1+a2: M(y) for y = y1 .. y1+len-1 into
- * M_dev[0..len) (int32), given carry = M(y1-1) (Sec. 3, step 5: "add up all
- * values of mu(y)").  Same limits and scratch rule as mertens_sieve_mu.
+ * M_dev[0..len) (int32), given carry = M(y1-1) (Sec. 3, step 5: the running
+ * sum of mu(y)).  Same limits and scratch rule as mertens_sieve_mu.
  * MERTENS_EOVERFLOW if some |M(y)| >= 2^31.
  */
 int mertens_sieve_M(uint64_t y1, uint64_t len, int64_t carry, int32_t *M_dev,
@@ -286,8 +286,8 @@ int mertens_sieve_M(uint64_t y1, uint64_t len, int64_t carry, int32_t *M_dev,
 
 /*
  * Performance parameters used for plans created afterwards (process-wide).
- * None of them changes any result -- only speed (Sec. 3: "all the various
- * constants and thresholds ... were tuned for peak performance").
+ * None of them changes any result -- only speed (Sec. 3 likewise tunes its
+ * constants and thresholds for speed alone).
  *   u_factor      automatic sieve limit
  *                 u = u_factor * (count * n)^(2/3) * count^(-1/5),
  *                 clamped to (floor(sqrt(n)), n] (Sec. 2: u = O(n^(2/3)),
