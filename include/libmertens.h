@@ -293,7 +293,7 @@ int mertens_sieve_M(uint64_t y1, uint64_t len, int64_t carry, int32_t *M_dev,
  *                 clamped to (floor(sqrt(n)), n] (Sec. 2: u = O(n^(2/3)),
  *                 batched u = O((nN)^(2/3)));             default 0.45
  *   dense_c       dense cut-off y_c ~ dense_c * sqrt(floor(n/x)) per entry
- *                 (the paper's regions 1/1' bound c1);     default 1.6
+ *                 (the paper's regions 1/1' bound c1);     default 1.4
  *   gather_scale  multiplies the automatic end of the shared-memory gather
  *                 range;                                   default 1.0
  *   block_cap     largest automatic sieve block (0 = 2^28, or 2^30 above

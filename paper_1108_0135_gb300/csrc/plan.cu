@@ -259,7 +259,7 @@ static void block_range(const mertens_plan_s *p, uint64_t b, uint64_t *y1, uint6
 // Tuning in force for new plans (mertens_set_tuning); MERTENS_* environment
 // variables override single fields for experiments.
 static std::mutex g_tune_mu;
-static mertens_tuning g_tuning = {0.45, 1.6, 1.0, 0};
+static mertens_tuning g_tuning = {0.45, 1.4, 1.0, 0};
 
 static mertens_tuning tuning_now()
 {
@@ -271,7 +271,7 @@ static double dense_factor(const mertens_tuning &t)
 {
     const char *e = getenv("MERTENS_DENSE_C");
     double c = e ? atof(e) : t.dense_c;
-    return c > 0 ? c : 1.6;
+    return c > 0 ? c : 1.4;
 }
 
 // Shape of one target (host only): X, y_max and the closed-form term counts.

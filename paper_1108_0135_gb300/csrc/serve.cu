@@ -24,6 +24,7 @@
 namespace mert {
 std::vector<uint64_t> plan_auto_u(const std::vector<uint64_t> &ns);
 size_t plan_device_bytes(mertens_plan_t p);
+double plan_dense_factor();
 }  // namespace mert
 
 using namespace mert;
@@ -67,7 +68,8 @@ size_t estimate_table_batch_bytes(const std::vector<uint64_t> &ns, uint64_t y_ma
 
 // Device memory a batch's plan will take, estimated from the plan's shapes
 // (entry arrays, one sieve block of int16 M, the divisor-magic table and the
-// squarefree list up to the dense cut-off ~1.6 sqrt(n)), with slack.
+// squarefree list up to the dense cut-off, dense_c sqrt(n), dense_c at least
+// 1.6), with slack.
 size_t estimate_batch_bytes(const std::vector<uint64_t> &ns)
 {
     double entries = 0, ymax = 0, nmax = 0;
@@ -79,7 +81,7 @@ size_t estimate_batch_bytes(const std::vector<uint64_t> &ns)
         nmax = std::max(nmax, (double)n);
     }
     const double L = std::min(ymax, ymax > 6.9e10 ? 1073741824.0 : 268435456.0);
-    const double ydense = 1.6 * std::sqrt(nmax) + 8192.0;
+    const double ydense = std::max(plan_dense_factor(), 1.6) * std::sqrt(nmax) + 8192.0;
     return (size_t)(110.0 * entries + 2.0 * L + 17.0 * ydense + 64.0e6);
 }
 

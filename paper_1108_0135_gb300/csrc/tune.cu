@@ -72,11 +72,11 @@ extern "C" int mertens_autotune(const mertens_u128 *n, size_t count, int runs,
         return status;
     }
     const double uf[] = {0.3, 0.45, 0.6, 0.8, 1.1};
-    const double dc[] = {1.2, 1.6, 2.1};
+    const double dc[] = {1.2, 1.4, 1.6, 2.1};
     const double gs[] = {0.5, 1.0, 2.0};
     for (int axis = 0; axis < 3; ++axis) {
         const double *vals = axis == 0 ? uf : (axis == 1 ? dc : gs);
-        const int nv = axis == 0 ? 5 : 3;
+        const int nv = axis == 0 ? 5 : (axis == 1 ? 4 : 3);
         mertens_tuning best_here = cur;
         double best_here_ms = cur_ms;
         for (int i = 0; i < nv; ++i) {

@@ -27,7 +27,7 @@ DENSE_S_PER_TERM = 0.58e-12
 GATHER_S_PER_TERM = 1.05e-12
 
 
-def work_density(y: np.ndarray, n: int, X: int, c: float = 1.6) -> np.ndarray:
+def work_density(y: np.ndarray, n: int, X: int, c: float = 1.4) -> np.ndarray:
     """Estimated seconds per unit y at y: the sieve, the dense terms of the
     entries whose cut-off c sqrt(k) is above y (a fraction 6/pi^2 of y are
     squarefree), and the gathered terms k/y^2 of the entries whose cut-off is
