@@ -599,8 +599,8 @@ def window_measure(stream):
 # kernel (profiles/), or None when the kernel changed since the capture.
 TRAFFIC_PER_LAUNCH = {
     "mu_sieve": 1.053e6 + 476.298e6,       # profiles/mu_sieve_byte_1e16.md (one 2^28-y block)
-    "update_dense": 989.370e6 + 5.861e6,   # profiles/dense_update_1e16.md
-    "update_gathered": 509.817e6 + 4.147e6,  # profiles/gather_tile_1e16.md (first block)
+    "update_dense": 864.412e6 + 6.018e6,   # profiles/dense_update_1e16.md (cut-off 1.4)
+    "update_gathered": 509.948e6 + 3.940e6,  # profiles/gather_tile_1e16.md (first block, cut-off 1.4)
 }
 
 SIX_OVER_PI2 = 6.0 / math.pi ** 2
