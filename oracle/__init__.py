@@ -56,6 +56,10 @@ def _load():
             lib.oracle_count_terms.argtypes = [u64, u64, ctypes.POINTER(u64),
                                                ctypes.POINTER(u64)]
             lib.oracle_count_terms.restype = ctypes.c_int
+            lib.oracle_window_sums.argtypes = [u64, u64, u64, u64, u64, u64, u64,
+                                               ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.POINTER(i64)]
+            lib.oracle_window_sums.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -118,3 +122,22 @@ def count_terms(n: int, u: int):
     if rc != 0:
         raise ValueError("oracle_count_terms failed")
     return int(d.value), int(g.value)
+
+
+def window_sums(n: int, u: int, y1: int, length: int, x_first: int = 1, x_last: int = 0):
+    """One y-window's carry-free share of the update (Sec. 2 split form):
+    (S, coef, mu_sum) for entries x_first..x_last (default: all X = n//u),
+    S and coef as uint64 arrays (mod 2^64).  The window's terms of entry x
+    are S[x] + M(y1-1) coef[x]; mu_sum is the window's sum of mu."""
+    lo, hi = _split(n)
+    if x_last == 0:
+        x_last = n // u
+    cnt = x_last - x_first + 1
+    S = np.zeros(max(cnt, 0), dtype=np.uint64)
+    coef = np.zeros(max(cnt, 0), dtype=np.uint64)
+    mus = ctypes.c_int64()
+    rc = _load().oracle_window_sums(lo, hi, u, y1, length, x_first, x_last, S.ctypes.data,
+                                    coef.ctypes.data, ctypes.byref(mus))
+    if rc != 0:
+        raise ValueError(f"oracle_window_sums(n={n}, u={u}, y1={y1}, len={length}) failed: {rc}")
+    return S, coef, int(mus.value)

@@ -24,6 +24,11 @@
  *                        distinct quotients floor(n/d).  It returns the
  *                        paper's array M(floor(n/x)), x = 1..X (Sec. 2).
  *   oracle_isqrt         floor(sqrt(v)) by bisection.
+ *   oracle_window_sums   one y-window's share of the split-form sums of
+ *                        every array entry, with M(y) taken relative to
+ *                        the window start (Sec. 2 split form, Sec. 3's
+ *                        block-by-block y axis); 128-bit k, so it reaches
+ *                        targets above 2^64.
  *
  * Reading of the garbled split formula (Sec. 2): for any integer t in [1, v],
  *   M(v) = 1 - sum_{x=2}^{floor(v/t)} M(floor(v/x))
@@ -35,7 +40,18 @@
  * the identity sum_{x=1}^n M(floor(n/x)) = 1 (Sec. 2) for every n up to 10^4,
  * the recursion against the plain table for every n up to 10^5 and sampled
  * n up to 10^9, the ratio 0.570591 at n = 7766842813 quoted in Sec. 1, and
- * closed forms (mu of primes, prime squares, products of two primes).
+ * closed forms (mu of primes, prime squares, products of two primes).  The
+ * bisection square root against Python's integer square root over the whole
+ * 128-bit range.  The window sums: windows covering [1, u) with chained
+ * carries resolve to the recursion's array; above 2^64, the direct
+ * coefficients telescope to floor(k/y1) - floor(k/(y2+1)), S by summation by
+ * parts, and gathered terms counted per y instead of per j, in Python
+ * integers.
+ *
+ * Reach: oracle_mertens_array needs the plain table up to floor(sqrt(n)) with
+ * L < 2^31, so it refuses n >= 2^62; oracle_window_sums has no such limit on
+ * n (only on the window: y2 < 2^62, len < 2^31) and is what reaches targets
+ * whose k needs two words.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -279,5 +295,86 @@ int oracle_count_terms(uint64_t n, uint64_t u, uint64_t *direct,
     }
     *direct = dsum;
     *gathered = gsum;
+    return 0;
+}
+
+/* One y-window's share of the update of the array algorithm (Sec. 2 split
+ * form at t = s+1; Sec. 3 walks the y axis block by block), for the entries
+ * x = x_first..x_last of target n = n_hi*2^64 + n_lo with sieve limit u.
+ *
+ * Entry x has k = floor(n/x), s = floor(sqrt(k)), and its update terms are
+ *   direct:   M(y) * (floor(k/y) - floor(k/(y+1)))  for y = 1..s,
+ *   gathered: M(floor(k/j))  for j = floor(k/u)+1 .. floor(k/(s+1)).
+ * The window is y in [y1, y2], y2 = y1+len-1.  Its M(y) is known only up to
+ * the carry C = M(y1-1), so with Mw(y) = sum_{t=y1}^{y} mu(t) (mu from the
+ * naive block sieve above) the window's terms are affine in C:
+ *   sum (Mw(y) + C) * c_y = S + C * coef.
+ * This returns, for every entry, S = the sum of Mw over its direct terms with
+ * y in the window (times their coefficients) plus its gathered terms with
+ * floor(k/j) in the window, and coef = the sum of those direct coefficients
+ * plus the number of those gathered terms, both mod 2^64; and *mu_sum =
+ * Mw(y2), the window's carry-out.  The gathered j with floor(k/j) in
+ * [y1, y2] are exactly floor(k/(y2+1)) < j <= floor(k/y1).  Every quotient
+ * is taken in 128 bits.  Returns 0 on success, -1 on bad arguments, -2 on
+ * memory. */
+int oracle_window_sums(uint64_t n_lo, uint64_t n_hi, uint64_t u, uint64_t y1,
+                       uint64_t len, uint64_t x_first, uint64_t x_last,
+                       uint64_t *S_out, uint64_t *coef_out, int64_t *mu_sum)
+{
+    u128 n = ((u128)n_hi << 64) | n_lo;
+    if (n == 0 || u == 0 || (u128)u > n || y1 == 0 || len == 0 ||
+        len >= ((uint64_t)1 << 31) || x_first == 0 || x_last < x_first ||
+        (u128)x_last > n / u)
+        return -1;
+    uint64_t y2 = y1 + len - 1;
+    if (y2 < y1 || y2 >= ((uint64_t)1 << 62))
+        return -1;
+    int8_t *mu = malloc(len);
+    int32_t *Mw = malloc(sizeof(int32_t) * len);
+    if (!mu || !Mw) {
+        free(mu);
+        free(Mw);
+        return -2;
+    }
+    if (oracle_mu_window(y1, len, mu) != 0) {
+        free(mu);
+        free(Mw);
+        return -2;
+    }
+    int64_t run = 0;
+    for (uint64_t i = 0; i < len; i++) {
+        run += mu[i];
+        Mw[i] = (int32_t)run;
+    }
+    *mu_sum = run;
+    free(mu);
+    for (uint64_t x = x_first; x <= x_last; x++) {
+        u128 k = n / x;
+        uint64_t s = oracle_isqrt_u128((uint64_t)k, (uint64_t)(k >> 64));
+        uint64_t S = 0, coef = 0;
+        /* direct terms, y in [y1, min(y2, s)] */
+        uint64_t ylast = y2 < s ? y2 : s;
+        for (uint64_t y = y1; y <= ylast; y++) {
+            u128 c = k / y - k / ((u128)y + 1);
+            S += (uint64_t)c * (uint64_t)(int64_t)Mw[y - y1];
+            coef += (uint64_t)c;
+        }
+        /* gathered terms, j in [floor(k/u)+1, floor(k/(s+1))] with
+         * floor(k/j) in [y1, y2] */
+        u128 jlo = k / u + 1, jhi = k / ((u128)s + 1);
+        u128 ja = k / ((u128)y2 + 1) + 1, jb = k / y1;
+        if (ja < jlo)
+            ja = jlo;
+        if (jb > jhi)
+            jb = jhi;
+        for (u128 j = ja; j <= jb; j++) {
+            u128 w = k / j;
+            S += (uint64_t)(int64_t)Mw[(uint64_t)(w - y1)];
+            coef += 1;
+        }
+        S_out[x - x_first] = S;
+        coef_out[x - x_first] = coef;
+    }
+    free(Mw);
     return 0;
 }
