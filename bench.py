@@ -363,7 +363,7 @@ def run_sharded(args, world, rank, local):
     barrier(world)
     wall_ms = (time.perf_counter() - t0) * 1e3 / args.steps
     clk = clocks.stop()
-    # each step ends in host copies (the exchange, resolve), so the device
+    # each step ends with the resolved array read to the host, so the device
     # interval between the events spans the whole step
     ms = ev0.elapsed_time(ev1) / args.steps
     ms_max = max_over_ranks(ms, world)
@@ -403,11 +403,11 @@ def run_sharded(args, world, rank, local):
             "rank0_window": list(window),
             "rank0_phases_ms": {k: round(v, 3) for k, v in phases.items()},
             "clocks": clk,
-            # every step already reads the window sums to the host, exchanges
-            # them and resolves from host memory: its host wall time is the
-            # end-to-end figure
+            # every step reads the window's mu sum (8 bytes) and, on rank 0,
+            # the resolved array to the host; the exchange stays on the device:
+            # the host wall time is the end-to-end figure
             "e2e": {"value": terms / (wall_max / 1e3), "unit": "update terms/s",
-                    "h2d_bytes_per_step": 16 * X, "d2h_bytes_per_step": 16 * X,
+                    "h2d_bytes_per_step": 8 * world, "d2h_bytes_per_step": 8 * X + 8,
                     "ms_per_step": wall_max},
             "gpu_launches": (kernels + 1) * args.steps,
             "roofline": (roofs[max(roofs, key=lambda k: phases[k])] if roofs else None),
@@ -581,43 +581,61 @@ def run_native(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
-def _timed_run(plan, stream):
-    """Seconds of one warm mertens_run (CUDA events on the launching stream)."""
+def _timed_run(plan, stream, repeats: int = 1):
+    """Seconds of warm mertens_run calls (CUDA events on the launching
+    stream): one untimed run, then `repeats` timed ones; returns the list."""
     import torch
     import paper_1108_0135_gb300 as pm
     pm.mertens_run(plan, stream)
     torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    pm.mertens_run(plan, stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    return e0.elapsed_time(e1) / 1e3
+    out = []
+    for _ in range(repeats):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pm.mertens_run(plan, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out.append(e0.elapsed_time(e1) / 1e3)
+    return out
 
 
-def batch_measure(stream):
+def batch_measure(stream, repeats: int = 3):
     """64 close targets 10^17 + i 10^9 in one plan (one sieve pass): wall time
-    and update terms/s; M(10^17) from Table 1 checked; one target alone (its
-    own u) timed beside it."""
+    (median of `repeats` warm runs) and update terms/s; M(10^17) from Table 1
+    checked; targets 0, 1 and 63 alone, with the batch's u, give the same
+    whole arrays; one target alone with its own u timed beside it."""
     import paper_1108_0135_gb300 as pm
     from paper_1108_0135_gb300 import workloads
     cfg = workloads.BATCH_1E17
     ns = cfg["n"]
     plan = pm.mertens_plan(ns, cfg["u"], 0)
     infos = [pm.mertens_plan_info(plan, i) for i in range(len(ns))]
-    t = _timed_run(plan, stream)
+    ts = _timed_run(plan, stream, repeats)
     m0, _ = pm.mertens_result(plan, 0)
+    batched = {i: pm.mertens_result(plan, i, entries=True) for i in (0, 1, 63)}
     pm.mertens_destroy(plan)
     assert m0 == -21830254, m0
+    for i, (mi, arr) in batched.items():
+        pa = pm.mertens_plan([ns[i]], infos[i]["u"], 0)
+        pm.mertens_run(pa, stream)
+        ma, arra = pm.mertens_result(pa, 0, entries=True)
+        pm.mertens_destroy(pa)
+        assert ma == mi and np.array_equal(arra, arr), i
+    t = float(np.median(ts))
     terms = sum(i["direct_terms"] + i["gathered_terms"] for i in infos)
     p1 = pm.mertens_plan([ns[0]])
-    t1 = _timed_run(p1, stream)
+    t1s = _timed_run(p1, stream, repeats)
     pm.mertens_destroy(p1)
-    return {"targets": len(ns), "wall_time_s": t, "update_terms_per_s": terms / t,
+    t1 = float(np.median(t1s))
+    return {"targets": len(ns), "wall_time_s": t, "wall_time_runs_s": ts,
+            "update_terms_per_s": terms / t,
             "queries_per_s": len(ns) / t, "u": infos[0]["u"], "X_each": infos[0]["X"],
             "M_n0": m0, "expected_table1": -21830254,
-            "one_target_alone_s": t1, "alone_x64_over_batch": 64 * t1 / t}
+            "alone_equals_batched": [0, 1, 63],
+            "one_target_alone_s": t1, "one_target_alone_runs_s": t1s,
+            "alone_x64_over_batch": 64 * t1 / t,
+            "alone_x64_over_batch_range": [64 * min(t1s) / max(ts), 64 * max(t1s) / min(ts)]}
 
 
 def window_measure(stream):
@@ -630,7 +648,7 @@ def window_measure(stream):
     plan = pm.mertens_plan_window(cfg["n"], cfg["y_first"], cfg["y_last"], cfg["u"],
                                   cfg["block_len"])
     info = pm.mertens_plan_info(plan, 0)
-    t = _timed_run(plan, stream)
+    t = _timed_run(plan, stream)[0]
     S, coef, mu = pm.mertens_window_result(plan, 0)
     pm.mertens_destroy(plan)
     ny = cfg["y_last"] - cfg["y_first"] + 1
@@ -642,13 +660,26 @@ def window_measure(stream):
             "entries_with_terms": terms, "mu_sum": mu}
 
 
-# DRAM bytes (read + write) per launch from one ncu capture of the current
-# kernel (profiles/), or None when the kernel changed since the capture.
-TRAFFIC_PER_LAUNCH = {
-    "mu_sieve": 1.053e6 + 476.298e6,       # profiles/mu_sieve_byte_1e16.md (one 2^28-y block)
-    "update_dense": 864.412e6 + 6.018e6,   # profiles/dense_update_1e16.md (cut-off 1.4)
-    "update_gathered": 509.948e6 + 3.940e6,  # profiles/gather_tile_1e16.md (first block, cut-off 1.4)
+# From ncu captures of the current kernel versions on the n = 10^16 workload
+# (one GB300, --clock-control none), per kernel class:
+#   dram_bytes_per_step: dram__bytes_read.sum + dram__bytes_write.sum summed
+#     over all of the class's launches in one run (a run of the capture, or
+#     one captured launch times the launches per run where every launch does
+#     the same work per y), None when a kernel of the class changed since;
+#   issue_active: smsp__issue_active.avg.pct_of_peak_sustained_active of the
+#     class's main kernel (share of cycles a scheduler issued an instruction);
+#   pipe: the busiest pipe of that kernel and its share of active cycles.
+NCU = {
+    "mu_sieve": {"kernel": "mu_sieve_byte_kernel", "dram_bytes_per_step": 150 * 477.351e6,
+                 "issue_active": 0.621, "pipe": ("alu", 0.463)},
+    "update_dense": {"kernel": "dense_update_kernel", "dram_bytes_per_step": 870.43e6,
+                     "issue_active": 0.485, "pipe": ("fmaheavy", 0.87)},
+    "update_gathered": {"kernel": "gather_tile_kernel", "dram_bytes_per_step": None,
+                        "issue_active": 0.886, "pipe": ("alu", 0.618)},
 }
+# Issue slots of the chip: 152 SMs x 4 schedulers x one warp instruction per
+# clock at the maximum SM clock.
+ISSUE_PEAK_WARP_INSTR_PER_S = 152 * 4 * 2070e6
 
 SIX_OVER_PI2 = 6.0 / math.pi ** 2
 
@@ -657,42 +688,50 @@ def rooflines(phases, stats, peaks, nblocks, ipk):
     """Roofline records per kernel class of the timed region.
 
     Every class here is bound by integer issue (no tensor cores, no floating
-    point; HBM traffic is ~2 B per sieved y).  Denominators are measured on
-    this device by mertens_probe_int_peaks (ipk):
+    point contraction; HBM traffic is about 2 B per sieved y).  MEASURED_PEAKS
+    holds no integer figure, so `peak` is the speed of the class's own inner
+    step, measured on this device by mertens_probe_int_peaks (ipk: independent
+    chains of that step on every SM) -- `frac` is the fraction of that
+    inner-step speed, not of a chip pipe peak.  Beside it, `issue` gives the
+    ncu issue-active share of the class's main kernel and its busiest pipe
+    (NCU above), against the chip's issue slots.
       update_dense: the update's inner step acc += mulhi64(m, 2k) >> l, in
-        terms/s (the 64x64 multiply-high runs on the FMA-heavy pipe; ncu
-        shows that pipe as the kernel's limiter).  Algorithmic terms:
-        squarefree y of the dense ranges ((6/pi^2) x the summed dense y-range).
+        terms/s.  Algorithmic terms: squarefree y of the dense ranges
+        ((6/pi^2) x the summed dense y-range).
       update_gathered: one term per gathered j, against the faster of that
         step and the shared-memory gather's float-estimate quotient step
         (the tile kernel takes the latter, the global path the former).
       mu_sieve: 32-bit ALU lane operations/s (LOP3 + IADD3 chains).
         Algorithmic operations: one per sieve update (y, p | y or p^2 | y
-        for every sieving prime p) plus two per y (decision + scan add)."""
+        for every sieving prime p) plus two per y (decision + scan add).
+    `achieved` and `traffic` are per step (all launches of the class)."""
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     mulhi_peak = ipk["mulhi_terms_per_s"] / 1e12
     alu_peak = 2.0 * ipk["alu_pairs_per_s"] / 1e12
     gather_peak = max(ipk["mulhi_terms_per_s"], ipk.get("fquot_terms_per_s", 0.0)) / 1e12
     work = {
         "mu_sieve": (stats["sieve_updates"] + 2.0 * stats["y_sieved"], alu_peak, "T int-op/s",
-                     "measured: LOP3+IADD3 chains on all SMs, 2 ops per pair"),
+                     "inner-step probe: LOP3+IADD3 chains on all SMs, 2 ops per pair"),
         "update_dense": (SIX_OVER_PI2 * stats["dense_y"], mulhi_peak, "T mulhi-terms/s",
-                         "measured: acc += mulhi64(m,2k) >> l chains on all SMs"),
+                         "inner-step probe: acc += mulhi64(m,2k) >> l chains on all SMs"),
         "update_gathered": (float(stats["gather_j"]), gather_peak, "T terms/s",
-                            "measured: the faster of the mulhi64 step and the float-estimate "
-                            "quotient step, chains on all SMs"),
+                            "inner-step probe: the faster of the mulhi64 step and the "
+                            "float-estimate quotient step, chains on all SMs"),
     }
-    launches = {"mu_sieve": nblocks, "update_dense": 1, "update_gathered": nblocks}
     out = {}
     for k, (v, peak, unit, src) in work.items():
         ms = phases.get(k, 0.0)
         if ms <= 0:
             continue
         achieved = v / (ms / 1e3) / 1e12
+        nc = NCU[k]
         out[k] = {"bound": "alu", "kernel": k, "achieved": achieved, "peak": peak,
                   "unit": unit, "frac": achieved / peak,
-                  "traffic": TRAFFIC_PER_LAUNCH.get(k),
-                  "launches_per_step": launches[k],
+                  "frac_of": "the class's inner-step speed measured by the probe",
+                  "traffic": nc["dram_bytes_per_step"], "traffic_per": "step",
+                  "issue": {"kernel": nc["kernel"], "ncu_issue_active": nc["issue_active"],
+                            "busiest_pipe": nc["pipe"][0], "pipe_active": nc["pipe"][1],
+                            "peak_warp_instr_per_s": ISSUE_PEAK_WARP_INSTR_PER_S},
                   "peak_source": f"{src} ({ipk['sms']} SMs, max SM clock {sm_mhz:.0f} MHz)"}
     return out
 

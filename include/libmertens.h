@@ -160,6 +160,41 @@ int mertens_plan_window(mertens_plan_t *out, const mertens_u128 *n, size_t count
 int mertens_resolve(mertens_u128 n, uint64_t u, const uint64_t *S, int64_t *M_out, void *stream);
 
 /*
+ * The exchange step on the device, for windows run on several devices (or
+ * in any order on one).  An exchange buffer holds 2 X int64 words: word
+ * 2(x-1) the low and word 2(x-1)+1 the high 32-bit half of entry x's 64-bit
+ * sum, so buffers can be added element-wise (an all-reduce SUM of int64 over
+ * up to 2^31 windows, in any backend) without signed overflow.
+ *
+ * mertens_window_accumulate -- adds target i's window sums of window plan
+ * `plan` (after its mertens_run), S_loc[x] + C coef[x] (mod 2^64), into the
+ * exchange buffer X2_dev, where the carry C = M(y_first - 1) is the sum of
+ * the mu sums of the windows below this one, mu_before[0..count) (host
+ * array; each window's mu sum is the *mu_sum of mertens_window_result).
+ * Sec. 2-3: every contribution of a window is affine in its carry.  Waits
+ * for the plan's last run (to read its sieve status), then enqueues the
+ * addition on `stream` and returns.
+ * X2_dev: device, 8-byte aligned, 2 X_i int64 words, owned by the caller and
+ * zeroed by the caller before the first window is added.
+ * Errors: MERTENS_EINVAL (NULL or unaligned buffer, bad index, not a window
+ * plan, mu_before NULL with count > 0), MERTENS_ENOTREADY (not run),
+ * a sieve status of the run (MERTENS_EOVERFLOW, MERTENS_ETIMEOUT),
+ * MERTENS_ECUDA.
+ *
+ * mertens_resolve_exchange -- mertens_resolve from an exchange buffer on the
+ * device: M_dev[x-1] = M(floor(n/x)), x = 1..X = floor(n/u), from the sums
+ * S[x] = X2_dev[2(x-1)] + 2^32 X2_dev[2(x-1)+1] (mod 2^64).  Both buffers are
+ * device memory owned by the caller (X2_dev 2 X int64 words, M_dev X int64
+ * words, 8-byte aligned).  Runs on `stream` and returns when done (its
+ * scratch is allocated through the allocator hook).  Errors: MERTENS_EINVAL,
+ * MERTENS_ENOMEM, MERTENS_ECUDA.
+ */
+int mertens_window_accumulate(mertens_plan_t plan, size_t i, const int64_t *mu_before,
+                              size_t count, int64_t *X2_dev, void *stream);
+int mertens_resolve_exchange(mertens_u128 n, uint64_t u, const int64_t *X2_dev, int64_t *M_dev,
+                             void *stream);
+
+/*
  * mertens_window_result -- wait for the last run of window plan `plan` and
  * return target i's partial sums: S_loc[x-1] and coef[x-1] for
  * x = 1..min(cap, X_i) (either may be NULL; uint64, mod 2^64), *len = X_i,
@@ -363,6 +398,22 @@ typedef struct {
 } mertens_int_peaks;
 int mertens_probe_int_peaks(mertens_int_peaks *out, void *stream);
 
+/*
+ * mertens_division_constants -- host only, no device needed: the
+ * invariant-divisor constants the kernels use for divisor d (Granlund and
+ * Montgomery, "Division by invariant integers using multiplication", PLDI
+ * 1994, Sec. 4), so that tests can hold them to integer division.
+ *   *m64, *l64: for 1 <= d < 2^63, floor(k/d) = mulhi64(m64, 2k) >> l64 for
+ *     every k < 2^63 (l64 = ceil(log2 d)).
+ *   *m32, *s32: for 2 <= d < 2^31, floor(v/d) = mulhi32(m32, v) >> s32 for
+ *     every v < 2^31 (both 0 for other d).
+ * Any output may be NULL.  Errors: MERTENS_EINVAL for d = 0 or d >= 2^63.
+ * The paper names precomputed multiply-and-shift constants for small
+ * divisors (Sec. 3); these are the library's own.
+ */
+int mertens_division_constants(uint64_t d, uint64_t *m64, uint32_t *l64, uint32_t *m32,
+                               uint32_t *s32);
+
 /* ---- serving: continuous batching of M(n) queries ---------------------- */
 
 /*
@@ -437,7 +488,9 @@ void mertens_server_destroy(mertens_server_t srv);
  * array inside the library, held on every GPU that loads the library until
  * the process exits.  Limits: 1 <= len <= 2^21 and y1 + len - 1 < 2^40,
  * otherwise MERTENS_EINVAL with an explanatory mertens_last_error().
- * The call allocates no device memory and no host heap memory.
+ * The call allocates no device memory and no host heap memory.  It sieves
+ * with the 16-bit log-sieve kernel (the allocating call takes the byte
+ * kernel where that one is exact); the results are the same.
  *
  * The first call on a device looks up the array's device address (with that
  * device current); make that first call before any stream capture on the

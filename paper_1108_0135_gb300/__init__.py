@@ -11,7 +11,8 @@ from ._lib import (  # noqa: F401
     mertens_last_error, mertens_plan, mertens_plan_info, mertens_plan_set_profiling,
     mertens_plan_window, mertens_window_result, mertens_table_create, mertens_table_info,
     mertens_plan_on_table, mertens_table_destroy, mertens_server_use_table, mertens_scan_extremes,
-    mertens_probe_int_peaks, mertens_resolve,
+    mertens_probe_int_peaks, mertens_resolve, mertens_window_mu_sum, mertens_window_accumulate,
+    mertens_resolve_exchange, mertens_division_constants,
     mertens_autotune, mertens_get_tuning, mertens_set_tuning,
     mertens_result, mertens_result_into, mertens_run, mertens_run_stats_get,
     mertens_server_create, mertens_server_destroy, mertens_server_poll, mertens_server_stats_get,

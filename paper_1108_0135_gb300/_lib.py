@@ -62,7 +62,8 @@ EXPORTS = [
     "mertens_server_destroy", "mertens_plan_window", "mertens_window_result",
     "mertens_table_create", "mertens_table_info", "mertens_plan_on_table", "mertens_table_destroy",
     "mertens_server_use_table", "mertens_scan_extremes", "mertens_probe_int_peaks",
-    "mertens_resolve",
+    "mertens_resolve", "mertens_window_accumulate", "mertens_resolve_exchange",
+    "mertens_division_constants",
 ]
 
 
@@ -139,6 +140,12 @@ def load():
         lib.mertens_scan_extremes.restype = c_int
         lib.mertens_resolve.argtypes = [mertens_u128, u64, P, P, P]
         lib.mertens_resolve.restype = c_int
+        lib.mertens_window_accumulate.argtypes = [P, sz, P, sz, P, P]
+        lib.mertens_window_accumulate.restype = c_int
+        lib.mertens_resolve_exchange.argtypes = [mertens_u128, u64, P, P, P]
+        lib.mertens_resolve_exchange.restype = c_int
+        lib.mertens_division_constants.argtypes = [u64, P, P, P, P]
+        lib.mertens_division_constants.restype = c_int
         lib.mertens_probe_int_peaks.argtypes = [ctypes.POINTER(mertens_int_peaks), P]
         lib.mertens_probe_int_peaks.restype = c_int
         lib.mertens_table_destroy.argtypes = [P]
@@ -325,6 +332,42 @@ def mertens_resolve(n: int, u: int, S, stream=None) -> np.ndarray:
     _check(load().mertens_resolve(u128(n), int(u), S.ctypes.data, out.ctypes.data,
                                   _stream(stream)), "mertens_resolve")
     return out
+
+
+def mertens_window_mu_sum(plan: int, i: int = 0) -> int:
+    """The window's mu sum M(y_last) - M(y_first - 1) alone (8 bytes read)."""
+    ln = ctypes.c_size_t()
+    mu = ctypes.c_int64()
+    _check(load().mertens_window_result(plan, i, None, None, 0, ctypes.byref(ln),
+                                        ctypes.byref(mu)), "mertens_window_result")
+    return int(mu.value)
+
+
+def mertens_window_accumulate(plan: int, i: int, mu_before, X2_dev, stream=None) -> None:
+    """Adds target i's window sums S_loc + C coef, C = sum(mu_before), into the
+    exchange buffer X2_dev (device, 2 X int64 words: low and high 32-bit
+    halves of each entry's sum)."""
+    mus = np.ascontiguousarray([int(v) for v in mu_before], dtype=np.int64)
+    _check(load().mertens_window_accumulate(plan, i, mus.ctypes.data if mus.size else None,
+                                            mus.size, _ptr(X2_dev), _stream(stream)),
+           "mertens_window_accumulate")
+
+
+def mertens_resolve_exchange(n: int, u: int, X2_dev, M_dev, stream=None) -> None:
+    """M(floor(n/x)), x = 1..X, into M_dev (device, X int64) from the
+    exchange buffer X2_dev (device, 2 X int64 halves)."""
+    _check(load().mertens_resolve_exchange(u128(n), int(u), _ptr(X2_dev), _ptr(M_dev),
+                                           _stream(stream)), "mertens_resolve_exchange")
+
+
+def mertens_division_constants(d: int) -> dict:
+    """The kernels' invariant-divisor constants for divisor d (host only)."""
+    m64, m32 = ctypes.c_uint64(), ctypes.c_uint32()
+    l64, s32 = ctypes.c_uint32(), ctypes.c_uint32()
+    _check(load().mertens_division_constants(int(d), ctypes.byref(m64), ctypes.byref(l64),
+                                             ctypes.byref(m32), ctypes.byref(s32)),
+           "mertens_division_constants")
+    return dict(m64=m64.value, l64=l64.value, m32=m32.value, s32=s32.value)
 
 
 def mertens_probe_int_peaks(stream=None) -> dict:

@@ -58,7 +58,6 @@ constexpr uint64_t kByteTileThrMin = 1ull << 26;
 
 // Error bits of the plan's device status word.
 constexpr uint32_t kErrMOverflow = 1u;   // |M(y)| did not fit int32
-constexpr uint32_t kErrBadIndex = 2u;    // a self-check found an index out of range
 
 // Bit length of v (0 for v = 0).
 __host__ __device__ __forceinline__ unsigned bitlen64(uint64_t v)

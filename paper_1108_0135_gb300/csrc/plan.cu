@@ -178,6 +178,7 @@ struct mertens_plan_s {
     uint64_t y_first = 1, y_last = 0;
     bool window = false;
     std::vector<uint64_t> coef;
+    uint64_t *dcoef = nullptr;  // the same on the device (window plans)
     // plans on a resident table: M(y), the divisor magics and the dense list
     // are the table's; targets n <= table y_max are read from it directly
     // (entry, y) pairs
@@ -975,6 +976,8 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
     p->dqs = p->alloc<QueryDev>(count);
     if (!p->wide.empty())
         p->dwide = p->alloc<WideEntry>(p->wide.size());
+    if (window)
+        p->dcoef = p->alloc<uint64_t>(E);
     for (auto &a : p->allocs)
         if (!a.first)
             rc = MERTENS_ENOMEM;
@@ -987,7 +990,7 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
                     !p->dcounter_dense || !p->dcounter_gather ||
                     !p->dgitems || !p->dcarry || !p->derr || !p->dcounter || !p->dMG ||
                     !p->ddl_m || !p->ddl_yo || !p->ddl_cnt || !p->dgroups || !p->ditems ||
-                    !p->dqs || (!p->wide.empty() && !p->dwide);
+                    !p->dqs || (!p->wide.empty() && !p->dwide) || (window && !p->dcoef);
     if (any_null)
         rc = MERTENS_ENOMEM;
     if (rc == MERTENS_OK && !table) {
@@ -1033,6 +1036,8 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
         if (!p->lookups.empty())
             cudaMemcpy(p->dlook, p->lookups.data(), p->lookups.size() * 8,
                        cudaMemcpyHostToDevice);
+        if (window)
+            cudaMemcpy(p->dcoef, p->coef.data(), E * 8, cudaMemcpyHostToDevice);
         if (!gtiles.empty())
             cudaMemcpy(p->dgtiles, gtiles.data(), gtiles.size() * sizeof(GatherTile),
                        cudaMemcpyHostToDevice);
@@ -1565,6 +1570,111 @@ int mertens_resolve(mertens_u128 n, uint64_t u, const uint64_t *S, int64_t *M_ou
     dev_free(al, dS, X * 8);
     dev_free(al, dK, X * 8);
     dev_free(al, dR, X * 8);
+    dev_free(al, dq, sizeof(QueryDev));
+    return rc;
+}
+
+int mertens_division_constants(uint64_t d, uint64_t *m64, uint32_t *l64, uint32_t *m32,
+                               uint32_t *s32)
+{
+    if (d == 0 || d >= (1ull << 63)) {
+        set_last_error("mertens_division_constants: need 1 <= d < 2^63");
+        return MERTENS_EINVAL;
+    }
+    if (m64)
+        *m64 = magic_of(d);
+    if (l64)
+        *l64 = magic_shift(d);
+    uint32_t m = 0;
+    unsigned sh = 0;
+    if (d >= 2 && d < (1ull << 31))
+        m = magic32_of((uint32_t)d, &sh);
+    if (m32)
+        *m32 = m;
+    if (s32)
+        *s32 = m ? sh : 0;
+    return MERTENS_OK;
+}
+
+int mertens_window_accumulate(mertens_plan_t p, size_t i, const int64_t *mu_before,
+                              size_t count, int64_t *X2_dev, void *stream)
+{
+    if (!p || i >= p->nq || !p->window || !X2_dev || ((uintptr_t)X2_dev & 7u) ||
+        (count && !mu_before)) {
+        set_last_error("mertens_window_accumulate: bad plan, index, buffer or mu sums, or not "
+                       "a window plan");
+        return MERTENS_EINVAL;
+    }
+    if (!p->ran) {
+        set_last_error("mertens_window_accumulate: mertens_run was not called");
+        return MERTENS_ENOTREADY;
+    }
+    if (!p->table) {
+        // the sieve's status words are read after the run has finished
+        if (cudaEventSynchronize(p->done) != cudaSuccess) {
+            set_last_error("mertens_window_accumulate: %s", cudaGetErrorString(cudaGetLastError()));
+            return MERTENS_ECUDA;
+        }
+        const uint32_t st = sieve_scratch_status(&p->pt);
+        if (st) {
+            set_last_error("mertens_window_accumulate: %s", sieve_status_text(st));
+            return sieve_status_code(st);
+        }
+    }
+    // C = M(y_first - 1): the windows below this one, summed mod 2^64
+    uint64_t C = 0;
+    for (size_t g = 0; g < count; ++g)
+        C += (uint64_t)mu_before[g];
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint64_t o = p->off[i];
+    if (cudaStreamWaitEvent(s, p->done, 0) != cudaSuccess ||
+        window_accumulate_enqueue(p->dS + o, p->dcoef + o, C, p->X[i], X2_dev, s) < 0) {
+        set_last_error("mertens_window_accumulate: %s", cudaGetErrorString(cudaGetLastError()));
+        return MERTENS_ECUDA;
+    }
+    return MERTENS_OK;
+}
+
+int mertens_resolve_exchange(mertens_u128 n, uint64_t u, const int64_t *X2_dev, int64_t *M_dev,
+                             void *stream)
+{
+    if (check_n(n, "mertens_resolve_exchange", 0) != MERTENS_OK || !X2_dev || !M_dev ||
+        ((uintptr_t)X2_dev & 7u) || ((uintptr_t)M_dev & 7u))
+        return MERTENS_EINVAL;
+    const u128 nn = to_u128(n);
+    if (check_u(nn, u) != MERTENS_OK || nn / u >= ((u128)1 << 32)) {
+        set_last_error("mertens_resolve_exchange: need floor(sqrt(n)) < u <= n and n/u < 2^32");
+        return MERTENS_EINVAL;
+    }
+    const uint64_t X = (uint64_t)(nn / u);
+    cudaStream_t s = (cudaStream_t)stream;
+    const Allocator al = current_allocator();
+    std::vector<uint64_t> K(X);
+    for (uint64_t x = 1; x <= X; ++x) {
+        const u128 k = nn / x;
+        K[x - 1] = k >= kTwo63 ? 0 : (uint64_t)k;  // only k == 1 is looked at
+    }
+    uint64_t *dS = (uint64_t *)dev_alloc(al, X * 8);
+    uint64_t *dK = (uint64_t *)dev_alloc(al, X * 8);
+    QueryDev *dq = (QueryDev *)dev_alloc(al, sizeof(QueryDev));
+    int rc = MERTENS_OK;
+    if (!dS || !dK || !dq)
+        rc = MERTENS_ENOMEM;
+    if (rc == MERTENS_OK) {
+        QueryDev q;
+        q.X = X;
+        q.off = 0;
+        if (cudaMemcpyAsync(dK, K.data(), X * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(dq, &q, sizeof q, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            halves_to_sums_enqueue(X2_dev, X, dS, s) < 0 ||
+            resolve_enqueue(dq, 1, dS, dK, (uint64_t *)M_dev, s) < 0 ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            rc = MERTENS_ECUDA;
+    }
+    if (rc == MERTENS_ECUDA)
+        set_last_error("mertens_resolve_exchange: %s", cudaGetErrorString(cudaGetLastError()));
+    dev_free(al, dS, X * 8);
+    dev_free(al, dK, X * 8);
     dev_free(al, dq, sizeof(QueryDev));
     return rc;
 }

@@ -594,6 +594,58 @@ __global__ void __launch_bounds__(1024) resolve_kernel(const QueryDev *__restric
 }
 
 // ---------------------------------------------------------------------------
+// Exchange of window sums (Sec. 2-3: a window's contributions are affine in
+// its carry C = M(y_first - 1)).  An exchange buffer holds every entry's
+// 64-bit sum as two int64 words, its low and its high 32-bit half, so that
+// element-wise sums of such buffers over up to 2^31 windows never overflow
+// a signed 64-bit word, whatever adds them.
+// ---------------------------------------------------------------------------
+// halves[2i] += low, halves[2i+1] += high half of S_loc[i] + C coef[i] (mod 2^64).
+__global__ void window_accumulate_kernel(const uint64_t *__restrict__ S,
+                                         const uint64_t *__restrict__ coef, uint64_t C,
+                                         uint64_t X, int64_t *__restrict__ halves)
+{
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < X;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t v = S[i] + C * coef[i];
+        halves[2 * i] += (int64_t)(v & 0xffffffffull);
+        halves[2 * i + 1] += (int64_t)(v >> 32);
+    }
+}
+
+// S[i] = halves[2i] + 2^32 halves[2i+1] (mod 2^64).
+__global__ void halves_to_sums_kernel(const int64_t *__restrict__ halves, uint64_t X,
+                                      uint64_t *__restrict__ S)
+{
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < X;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        S[i] = (uint64_t)halves[2 * i] + ((uint64_t)halves[2 * i + 1] << 32);
+}
+
+static unsigned grid_for(uint64_t n)
+{
+    const uint64_t b = (n + 255) / 256;
+    return (unsigned)(b < 152 * 16 ? (b ? b : 1) : 152 * 16);
+}
+
+int window_accumulate_enqueue(const uint64_t *S, const uint64_t *coef, uint64_t C, uint64_t X,
+                              int64_t *halves, cudaStream_t s)
+{
+    if (X == 0)
+        return 0;
+    window_accumulate_kernel<<<grid_for(X), 256, 0, s>>>(S, coef, C, X, halves);
+    return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
+int halves_to_sums_enqueue(const int64_t *halves, uint64_t X, uint64_t *S, cudaStream_t s)
+{
+    if (X == 0)
+        return 0;
+    halves_to_sums_kernel<<<grid_for(X), 256, 0, s>>>(halves, X, S);
+    return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
+// ---------------------------------------------------------------------------
 // Launchers.
 // ---------------------------------------------------------------------------
 int magic_table_enqueue(uint64_t *MG, uint64_t nd, cudaStream_t s)

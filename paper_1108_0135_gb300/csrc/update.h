@@ -152,6 +152,12 @@ int dense_update_enqueue(const DenseArgs &a, cudaStream_t s);
 int sparse_block_enqueue(const SparseBlockArgs &b, const SparseArgs &a, uint32_t *scan_scratch,
                          cudaStream_t s);
 int gather_tiles_enqueue(const GatherArgs &a, cudaStream_t s);
+// Exchange buffers (two int64 words per entry: the low and the high 32-bit
+// half of its 64-bit sum): add S_loc + C coef of a window; turn one back into
+// 64-bit sums.
+int window_accumulate_enqueue(const uint64_t *S, const uint64_t *coef, uint64_t C, uint64_t X,
+                              int64_t *halves, cudaStream_t s);
+int halves_to_sums_enqueue(const int64_t *halves, uint64_t X, uint64_t *S, cudaStream_t s);
 int resolve_enqueue(const QueryDev *qs, uint32_t nq, const uint64_t *S, const uint64_t *K,
                     uint64_t *R, cudaStream_t s);
 

@@ -3,11 +3,12 @@
 Every window's contribution to an entry's update sum is affine in the
 window's carry M(y_first - 1) (Sec. 2-3: direct and gathered terms are sums
 of M(y) = M_loc(y) + carry), so the ranks run disjoint windows of
-[1, y_max] independently through window plans, which return S_loc, the
-coefficient of the carry and the window's mu sum.  The exchange is an
-all-gather of the mu sums (a rank's carry is the sum of those before it) and
-one all-reduce of the entries' sums S = sum over ranks of S_loc + C coef
-(mod 2^64); rank 0 then resolves.  Windows are cut at equal estimated work
+[1, y_max] independently through window plans, which keep S_loc and the
+coefficient of the carry on the device.  The exchange is an all-gather of
+the windows' mu sums (a rank's carry is the sum of those before it), the
+library's addition of S_loc + C coef (mod 2^64) into a device buffer, and one
+all-reduce of those buffers; rank 0 then resolves from its device buffer.
+Nothing of the method's arithmetic runs here.  Windows are cut at equal estimated work
 (the sieve is uniform in y, the update terms crowd at small y).
 """
 from __future__ import annotations
@@ -59,51 +60,68 @@ def window_bounds(n: int, u: int, world: int):
     return [(cuts[g], cuts[g + 1] - 1) for g in range(world)]
 
 
-def combine(S_loc: np.ndarray, coef: np.ndarray, mu_sum: int, rank: int, world: int,
-            device=None) -> np.ndarray:
-    """The exchange step.  Every rank passes its window's S_loc, coef and mu
-    sum; every rank gets S = sum_g (S_loc,g + C_g coef_g) mod 2^64 with
-    C_g = sum_{h<g} mu_h.  The all-reduce carries the 32-bit halves of the
-    64-bit sums, so no backend sees a signed overflow."""
+def exchange(accumulate, mu_sum: int, X: int, rank: int, world: int, device=None):
+    """The exchange step; this function only moves bytes.  The windows' mu
+    sums (8 bytes per rank) are all-gathered; `accumulate(mu_before, buf)`
+    -- the library's mertens_window_accumulate, which forms the carry
+    C = sum(mu_before) and adds S_loc + C coef (mod 2^64) on the device --
+    fills a zeroed exchange buffer of 2 X int64 words (the low and high 32-bit
+    halves of every entry's sum); one all-reduce (SUM) of those buffers gives
+    every rank the whole update sums, with no signed overflow in any backend.
+    Returns the buffer (on `device`)."""
     import torch
-    import torch.distributed as dist
 
-    mus = [torch.zeros(1, dtype=torch.int64, device=device) for _ in range(world)]
-    dist.all_gather(mus, torch.tensor([int(mu_sum)], dtype=torch.int64, device=device))
-    carry = sum(int(m.item()) for m in mus[:rank])
-    part = S_loc.astype(np.uint64) + np.uint64(carry % 2**64) * coef.astype(np.uint64)
-    halves = np.stack([part & np.uint64(0xFFFFFFFF), part >> np.uint64(32)]).astype(np.int64)
-    t = torch.from_numpy(halves).to(device)
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    h = t.cpu().numpy().astype(np.uint64)
-    return (h[1] << np.uint64(32)) + h[0]
+    buf = torch.zeros(2 * X, dtype=torch.int64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+
+        mus = [torch.zeros(1, dtype=torch.int64, device=device) for _ in range(world)]
+        dist.all_gather(mus, torch.tensor([int(mu_sum)], dtype=torch.int64, device=device))
+        before = [int(m.item()) for m in mus[:rank]]
+    else:
+        before = []
+    accumulate(before, buf)
+    if world > 1:
+        dist.all_reduce(buf, op=dist.ReduceOp.SUM)
+    return buf
 
 
 class ShardedTarget:
     """A target prepared for repeated sharded runs: this rank's window plan
-    is made once; step() runs it, exchanges, and resolves on rank 0."""
+    is made once; step() runs it, exchanges on the device, and resolves on
+    rank 0 from the device buffer."""
 
     def __init__(self, n: int, u: int, block_len: int = 0, rank: int = 0, world: int = 1,
                  device=None):
-        self.n, self.u, self.rank, self.world, self.device = int(n), int(u), rank, world, device
+        import torch
+
+        self.n, self.u, self.rank, self.world = int(n), int(u), rank, world
+        self.device = device if device is not None else torch.device("cuda")
         self.X = self.n // self.u
         self.window = window_bounds(self.n, self.u, world)[rank]
         y1, y2 = self.window
         self.plan = L.mertens_plan_window([self.n], y1, y2, self.u, block_len) if y2 >= y1 else 0
 
     def step(self, stream=None):
+        """One sharded run; rank 0 returns M(floor(n/x)), x = 1..X (int64
+        numpy array), the other ranks None."""
+        import torch
+
+        mu = 0
         if self.plan:
             L.mertens_run(self.plan, stream)
-            S_loc, coef, mu = L.mertens_window_result(self.plan, 0)
-        else:
-            S_loc = np.zeros(self.X, dtype=np.uint64)
-            coef = np.zeros(self.X, dtype=np.uint64)
-            mu = 0
-        S = combine(S_loc, coef, mu, self.rank, self.world, self.device) if self.world > 1 \
-            else S_loc
+            mu = L.mertens_window_mu_sum(self.plan, 0)
+
+        def accumulate(before, buf):
+            if self.plan:
+                L.mertens_window_accumulate(self.plan, 0, before, buf, stream)
+
+        buf = exchange(accumulate, mu, self.X, self.rank, self.world, self.device)
         if self.rank != 0:
             return None
-        return L.mertens_resolve(self.n, self.u, S, stream)
+        M = torch.empty(self.X, dtype=torch.int64, device=self.device)
+        L.mertens_resolve_exchange(self.n, self.u, buf, M, stream)
+        return M.cpu().numpy()
 
     def close(self):
         if self.plan:

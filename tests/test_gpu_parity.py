@@ -323,6 +323,56 @@ def test_batch_of_close_targets_1e17(table1):
         assert res[i][1][X - 1] == oracle.mertens(ns[i] // X, L=10**8), i
 
 
+@pytest.fixture(scope="module")
+def batch_1e17():
+    """The 64-target batch n_i = 10^17 + i 10^9 in one plan (one sieve pass),
+    with the automatic batch u: every target's whole array and plan info."""
+    cfg = workloads.BATCH_1E17
+    ns = cfg["n"]
+    plan = pm.mertens_plan(ns, cfg["u"], 0)
+    try:
+        pm.mertens_run(plan)
+        res = [pm.mertens_result(plan, i, entries=True) for i in range(len(ns))]
+        infos = [pm.mertens_plan_info(plan, i) for i in range(len(ns))]
+    finally:
+        pm.mertens_destroy(plan)
+    return ns, res, infos
+
+
+def test_batch_1e17_full_size_table1(batch_1e17, table1):
+    ns, res, infos = batch_1e17
+    assert len(ns) == 64 and ns[0] == 10**17
+    assert res[0][0] == table1[10**17] == -21830254
+    # one u for the whole batch (Sec. 2: close targets share the sieve)
+    assert len({i["u"] for i in infos}) == 1
+
+
+@pytest.mark.parametrize("part", range(4))
+def test_batch_1e17_full_size_alone_equals_batched(batch_1e17, part):
+    """Each of the 64 targets alone, with the batch's u, gives the same whole
+    array as in the batch (16 targets per part)."""
+    ns, res, infos = batch_1e17
+    for i in range(16 * part, 16 * part + 16):
+        m1, arr1 = gpu_array(ns[i], infos[i]["u"])
+        assert res[i][0] == m1, i
+        assert np.array_equal(res[i][1], arr1), i
+
+
+@pytest.mark.parametrize("i", [1, 63])
+def test_batch_1e17_full_size_entries_against_oracle(batch_1e17, i):
+    """Targets 1 and 63: M(n_i) by Table 1's neighbour is not printed, so the
+    entries with the smallest k (about 7e11, the oracle's Sec. 2 recursion at
+    a fraction of a second each) are compared one by one: the last two and
+    six seeded ones with k <= 2e12."""
+    ns, res, _ = batch_1e17
+    n, arr = ns[i], res[i][1]
+    X = len(arr)
+    rng = np.random.default_rng(1000 + i)
+    xs = [X, X - 1] + [int(v) for v in rng.integers(n // (2 * 10**12), X, size=6)]
+    for x in xs:
+        assert arr[x - 1] == oracle.mertens(n // x, L=10**8), (i, x)
+
+
 # ---- two-word entries (k >= 2^63) ----------------------------------------------
 # MERTENS_WIDE_FROM moves the bound above which an entry takes the two-word
 # kernel, so that kernel can be compared with the oracle where the oracle is
@@ -364,6 +414,10 @@ def test_two_word_target_1e20(table1):
     assert m == table1[n] == 461113106
     X = len(arr)
     assert arr[X - 1] == oracle.mertens(n // X, L=2 * 10**7)
+    # Sec. 5: one large run also yields the smaller Table 1 values as array
+    # entries, M(floor(n/x)): x = 10 (a two-word entry), 100, 1000, 10^4
+    for x in (10, 100, 1000, 10**4):
+        assert arr[x - 1] == table1[n // x], x
 
 
 @pytest.mark.parametrize("n", [11609864264058592345, 10**19])
@@ -372,6 +426,11 @@ def test_two_word_targets_paper_values(n, table1):
     above 2^63 (entry x = 1 takes the two-word kernel)."""
     m, arr = gpu_array(n)
     assert m == table1[n]
+    # Sec. 5's self-consistency: entries x = 10, 100, 1000 of the 10^19 run
+    # are M(10^18), M(10^17), M(10^16) of Table 1
+    if n == 10**19:
+        for x in (10, 100, 1000):
+            assert arr[x - 1] == table1[n // x], x
     # the entries with the smallest k, by the oracle recursion
     X = len(arr)
     for x in (X, X - 1, X - 1000):
@@ -429,6 +488,40 @@ def test_windows_partition_equals_whole_run(wide_from, monkeypatch):
     assert np.array_equal(got, oracle.mertens_array(n, n // u, L=10**8))
 
 
+@pytest.mark.parametrize("wide_from", [None, 10**11])
+def test_window_accumulate_and_resolve_on_device(wide_from, monkeypatch):
+    """The device exchange: windows of a partition, each added into one
+    exchange buffer by mertens_window_accumulate with the mu sums of the
+    windows below it (the carry), resolve from the buffer on the device --
+    the same array as a whole run and as the oracle."""
+    if wide_from:
+        monkeypatch.setenv("MERTENS_WIDE_FROM", str(wide_from))
+    n, u = 10**12 + 12345, 10**8
+    m, arr = gpu_array(n, u, 2**22)
+    ymax = pm.mertens_describe(n, u)["y_max"]
+    cuts = [1, 700_001, 5_000_001, ymax + 1]
+    X = n // u
+    buf = torch.zeros(2 * X, dtype=torch.int64, device="cuda")
+    mus = []
+    # windows added in reverse order: the sum does not depend on it
+    plans = []
+    try:
+        for (a, b), bl in zip(zip(cuts[:-1], cuts[1:]), [2**18, 2**20 + 3, 0]):
+            plans.append(pm.mertens_plan_window([n], a, b - 1, u, bl))
+            pm.mertens_run(plans[-1])
+            mus.append(pm.mertens_window_mu_sum(plans[-1], 0))
+        for g in reversed(range(len(plans))):
+            pm.mertens_window_accumulate(plans[g], 0, mus[:g], buf)
+    finally:
+        for p in plans:
+            pm.mertens_destroy(p)
+    M = torch.empty(X, dtype=torch.int64, device="cuda")
+    pm.mertens_resolve_exchange(n, u, buf, M)
+    got = M.cpu().numpy()
+    assert np.array_equal(got, arr)
+    assert np.array_equal(got, oracle.mertens_array(n, X, L=10**8))
+
+
 def test_sharded_target_one_rank_equals_whole_run():
     """shard.ShardedTarget with one rank: the window [1, y_max] through a
     window plan, then mertens_resolve on its sums, equals a whole run."""
@@ -473,6 +566,51 @@ def test_window_two_word_target_at_1e13():
     got_S = {int(i) + 1: int(v) for i, v in enumerate(S) if v}
     assert got_c == want_c
     assert got_S == {x: v for x, v in want_S.items() if v}
+
+
+def _window_plan_sums(n, u, y1, length, block_len):
+    plan = pm.mertens_plan_window([n], y1, y1 + length - 1, u, block_len)
+    try:
+        pm.mertens_run(plan)
+        return pm.mertens_window_result(plan, 0)
+    finally:
+        pm.mertens_destroy(plan)
+
+
+def test_window_two_word_full_block_at_1e13_against_oracle():
+    """One whole 2^28-y block of the n = 10^20 window (u = 2.15e13, from
+    y = 10^13): every entry's carry-free sum and coefficient equal the
+    oracle's 128-bit window sums (entries x <= 10 are two-word)."""
+    cfg = workloads.WINDOW_1E20
+    n, u, y1, L = cfg["n"][0], cfg["u"], cfg["y_first"], cfg["block_len"]
+    S, coef, mu = _window_plan_sums(n, u, y1, L, L)
+    oS, oc, omu = oracle.window_sums(n, u, y1, L)
+    assert mu == omu
+    assert len(S) == len(oS) == n // u
+    assert np.array_equal(coef, oc)
+    assert np.array_equal(S, oS)
+    assert int(np.count_nonzero(oc[:10])) > 0      # two-word entries have terms here
+
+
+def test_window_two_word_direct_terms_against_oracle():
+    """A 2^20-y window at y = 3e9 of n = 10^20: entries x <= 11 have
+    s = floor(sqrt(k)) above it, so it holds only their direct terms
+    M(y)(floor(k/y) - floor(k/(y+1))) -- with 128-bit quotients for x <= 10 --
+    and gathered terms of the entries x >= 129.  Compared with the oracle's
+    window sums.  Entries 11..128 are left out: their dense cut-off
+    (about 1.4 sqrt(k), shared by groups of 32 entries) lies at or above the
+    window, where the update takes the mu-form of the same terms, whose
+    carry-free part differs by a boundary term."""
+    n, u = 10**20, workloads.WINDOW_1E20["u"]
+    y1, L = 3 * 10**9, 2**20
+    S, coef, mu = _window_plan_sums(n, u, y1, L, L)
+    oS, oc, omu = oracle.window_sums(n, u, y1, L)
+    assert mu == omu
+    x = np.arange(1, n // u + 1)
+    keep = (x <= 10) | (x >= 129)
+    assert np.array_equal(coef[keep], oc[keep])
+    assert np.array_equal(S[keep], oS[keep])
+    assert all(int(oc[i]) > L for i in range(10))   # direct coefficients of the two-word entries
 
 
 # ---- interval scan: extremes of M(y) and M(y)/sqrt(y) ---------------------------

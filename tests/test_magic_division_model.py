@@ -82,3 +82,20 @@ def test_a_smaller_shift_breaks():
         k = ((2**63 - 1) // d) * d - 1          # the largest k one below a multiple
         bad += div64(k, m, l) != k // d
     assert bad > 0
+
+
+def test_library_constants_are_these():
+    """The built library's own constants (mertens_division_constants: the
+    restoring long division on the host side of the kernels' set-up) equal
+    the ones modelled above, on the same divisors; no GPU is needed."""
+    import paper_1108_0135_gb300 as pm
+
+    rng = np.random.default_rng(1108)
+    ds = _divisors(rng, 40) + [2**62 + 1, 2**63 - 1, 3 * 2**60 + 7]
+    for d in ds:
+        c = pm.mertens_division_constants(d)
+        assert (c["m64"], c["l64"]) == magic64(d), d
+        if 2 <= d < 2**31:
+            assert (c["m32"], c["s32"]) == magic32(d), d
+        else:
+            assert c["m32"] == 0 and c["s32"] == 0, d

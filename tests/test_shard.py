@@ -3,9 +3,13 @@
 Each rank computes its window's carry-free pieces with a plain reference of
 the Sec. 2 split form (direct terms M(y)(floor(k/y) - floor(k/(y+1))) for
 y <= s, gathered terms M(floor(k/j)) for floor(X/x) < j <= floor(k/(s+1))),
-on M(y) from the oracle's table; the library's exchange step
-(paper_1108_0135_gb300.shard.combine) and a host resolve must give the
-oracle's array.  The window cuts come from shard.window_bounds.
+on M(y) from the oracle's table; the exchange step
+(paper_1108_0135_gb300.shard.exchange: all-gather of the mu sums, the
+addition of S_loc + C coef into a buffer of 32-bit halves, all-reduce) and a
+host resolve must give the oracle's array.  On a GPU the addition is the
+library's mertens_window_accumulate; here, without one, a plain stand-in with
+the same contract fills the buffer.  The window cuts come from
+shard.window_bounds.
 """
 import math
 import os
@@ -68,9 +72,20 @@ def _worker(rank, world, port, n, u, out_path):
         M = oracle.mertens_table(n + 1)
         a, b = shard.window_bounds(n, u, world)[rank]
         S_loc, coef, mu = _window_pieces(n, u, a, b, M)
-        S = shard.combine(S_loc, coef, mu, rank, world)
+
+        def accumulate(before, buf):
+            # the contract of mertens_window_accumulate, in Python integers
+            C = sum(before)
+            for i in range(len(S_loc)):
+                v = (int(S_loc[i]) + C * int(coef[i])) % 2**64
+                buf[2 * i] += v & 0xFFFFFFFF
+                buf[2 * i + 1] += v >> 32
+
+        buf = shard.exchange(accumulate, mu, n // u, rank, world, torch.device("cpu"))
         if rank == 0:
-            np.save(out_path, _resolve(n, S))
+            h = buf.numpy()
+            S = [(int(h[2 * i]) + (int(h[2 * i + 1]) << 32)) % 2**64 for i in range(n // u)]
+            np.save(out_path, _resolve(n, np.array(S, dtype=np.uint64)))
     finally:
         dist.destroy_process_group()
 

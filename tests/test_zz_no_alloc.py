@@ -36,7 +36,10 @@ def allocating(y1, length, carry):
 def test_noalloc_equals_allocating_entry_point_on_consecutive_calls():
     # two calls in a row with different windows: the second reuses (and must
     # fully overwrite) the scratch the first one left behind
-    for y1, length, carry in [(10**9 + 7, 300_011, 123_456), (1, 1 << 21, 0)]:
+    # the last window ends just below the stated limit y < 2^40, where the
+    # allocating call takes the byte sieve and this one the 16-bit sieve
+    for y1, length, carry in [(10**9 + 7, 300_011, 123_456), (1, 1 << 21, 0),
+                              ((1 << 40) - (1 << 21), 1 << 21, 0)]:
         out = torch.full((length,), -7, dtype=torch.int32, device="cuda")
         pm.mertens_sieve_M_noalloc(y1, length, carry, out)
         torch.cuda.synchronize()
