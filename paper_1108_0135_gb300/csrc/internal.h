@@ -50,6 +50,16 @@ struct PrimeTable {
     uint64_t *bucket = nullptr;   // tiles x bucket_cap
     uint32_t *gsq = nullptr;      // one bit per y of a block, whole tiles
     uint32_t *perr = nullptr;     // status bits of the persistent kernel
+    // byte sieve at weight scale 2 (square flag in bit 7): its prime records
+    // (as pq, with w2(p) = the odd integer nearest 2 log2 p), its pattern, and
+    // per-tile lists of the multiples of p^2 (p >= 8192) of a block
+    uint4 *pq2 = nullptr;
+    uint4 *pat2 = nullptr;        // 16 phase copies: 2, 3, 5, 7 (base 1, flags of their squares)
+    uint4 *rec = nullptr;         // per block, p >= 512: {p, m32(p), y1 mod p, s(p) | w2 << 8}
+    uint2 *rec2 = nullptr;        // per block, 512 <= p < 8192: {y1 mod p^2 | s << 26, m32(p^2)}
+    uint32_t sq_cap = 0;          // list entries per tile
+    uint32_t *sqcnt = nullptr;    // tiles of scratch_len
+    uint32_t *sqlist = nullptr;   // tiles x sq_cap
     // host copy of the primes (for counting primes <= a bound)
     uint32_t *host_p = nullptr;
     Allocator al;

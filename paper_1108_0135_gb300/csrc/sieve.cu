@@ -617,6 +617,438 @@ __global__ void __launch_bounds__(kSieveThreads, 1) mu_sieve_byte_kernel(ByteArg
 }
 
 // ---------------------------------------------------------------------------
+// a1 + a2, byte variant at weight scale 2 with the square flag in bit 7.
+// Same method (Sec. 3 log sieve, then the prefix sum).  The byte of y holds
+//     1 + sum over the distinct sieving primes p | y of w2(p),
+// w2(p) the odd integer nearest 2 log2 p, plus 128 when a square of a
+// sieving prime divides y.  The sum stays below 128 for y < 2^54
+// (1 + 2 log2 y + E), so the square flag is set by atomicOr at any time and
+// no add ever carries into it or out of the byte; the tile needs no separate
+// square array, which lets two or three CTAs share an SM.
+// Exactness: with A the weight sum, c = 1 gives A >= 2 log2 y - E and c > 1
+// gives A <= 2 log2 y - 2 log2 P + E (E the summed rounding, at most the
+// number of distinct prime factors), so the threshold T = 2 log2 y - log2 P
+// separates them with log2 P - E units either side; the host takes this
+// kernel only where that is at least 2.5, and then any integer threshold in
+// [T - 2, T] is exact.  Tiles at y >= 2^26 take one even threshold thr per
+// tile: W = (byte & 127) + 126 - thr puts A > thr into bit 7 of W and the
+// count parity (xor 1) into bit 0, so mu = -1 exactly when they differ.
+//
+// Work of a tile:
+//   * the pre-sieve pattern: primes 2, 3, 5, 7 with the base 1 and the flags
+//     of 4, 9, 25, 49 (period 44100, one bulk asynchronous copy);
+//   * primes 11 <= p < 512: a warp over the multiples of one prime, largest
+//     jobs first;
+//   * primes p >= 512: a lane per prime, two per lane, the hits of primes
+//     below a ninth of the tile four at a time with loop-invariant shifted
+//     weights; the square of a prime below 8192 per lane, those of larger
+//     primes from a per-block list (at most sixteen multiples of p^2 per
+//     prime in a block of up to 2^30 y).
+// ---------------------------------------------------------------------------
+struct T2Args {
+    uint64_t y1;
+    uint32_t len;          // <= 2^30
+    uint32_t np;           // primes used (all p <= P)
+    uint32_t np_lane;      // [4, np_lane): 11 <= p < 512, a warp per prime
+    uint32_t np_list;      // [np_list, np): p >= 8192, squares from the block's list
+    float thr_half;        // log2 P
+    const uint4 *pq;       // {p, m32(p), m32(p^2) or 0, s(p) | s(p^2) << 8 | w2(p) << 16}
+    const uint4 *rec;      // per block, p >= 512: {p, m32(p), y1 mod p, s(p) | w2(p) << 8}
+    const uint2 *rec2;     // per block, 512 <= p < 8192: {y1 mod p^2 | s(p^2) << 26, m32(p^2)}
+    const uint32_t *r;     // y1 mod p
+    const uint64_t *r2;    // y1 mod p^2
+    const uint4 *pat;      // 16 phase copies of the 2, 3, 5, 7 pattern
+    uint32_t *sqcnt;       // per tile: entries in the square list (cleared after use)
+    const uint32_t *sqlist;// per tile: sqcap offsets of multiples of p^2, p >= 8192
+    uint32_t sqcap;
+    int16_t *Mloc;
+    int32_t *segsum;
+    int8_t *mu_out;
+    uint64_t mu_base, mu_end;
+    uint32_t extra_tx;     // bytes announced beyond the copy (0; tests of the bounded wait)
+    uint32_t *err;         // kErrTimeout / kErrBucket
+};
+
+constexpr uint32_t kT2JobsMax = 128;          // descriptor jobs (93: the primes 11 .. 509)
+constexpr uint32_t kPat2Len = 142416;         // >= 44100 + 98304, multiple of 16
+constexpr uint32_t kT2LaneMin = 512;          // primes from here: a lane per prime
+constexpr uint32_t kT2ListMin = 8192;         // primes from here: squares from the list
+constexpr uint64_t kT2MinTile = 65536;        // smallest tile (square-list scratch)
+// Status bit: a bucket or a square list overflowed its capacity.
+constexpr uint32_t kErrBucket = 4u;
+
+// Per block: y1 mod p and y1 mod p^2 of every sieving prime, and the
+// multiples of p^2 (p >= 8192, index >= list0) as offsets into per-tile lists.
+__global__ void t2_block_prep_kernel(uint64_t y1, uint32_t np, const uint4 *__restrict__ pq,
+                                     uint32_t *__restrict__ r, uint64_t *__restrict__ r2,
+                                     uint32_t lane0, uint4 *__restrict__ rec,
+                                     uint2 *__restrict__ rec2, uint32_t list0, uint32_t len,
+                                     uint32_t tile, uint32_t *__restrict__ cnt,
+                                     uint32_t *__restrict__ list, uint32_t cap,
+                                     uint32_t *__restrict__ err)
+{
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= np)
+        return;
+    const uint4 pr = pq[t];
+    const uint64_t q = pr.x, q2 = q * q;
+    const uint32_t rq = (uint32_t)(y1 % q);
+    r[t] = rq;
+    const uint64_t rem = y1 % q2;
+    r2[t] = rem;
+    if (t >= lane0) {
+        rec[t] = make_uint4(pr.x, pr.y, rq, (pr.w & 255u) | ((pr.w >> 16) << 8));
+        if (t < list0)  // q < 8192: q^2 < 2^26, its magic and shift
+            rec2[t] = make_uint2((uint32_t)rem | (((pr.w >> 8) & 255u) << 26), pr.z);
+    }
+    if (t < list0)
+        return;
+    for (uint64_t o = rem ? q2 - rem : 0; o < len; o += q2) {
+        const uint32_t ti = (uint32_t)(o / tile);
+        const uint32_t slot = atomicAdd(&cnt[ti], 1u);
+        if (slot < cap)
+            list[(size_t)ti * cap + slot] = (uint32_t)(o - (uint64_t)ti * tile);
+        else
+            atomicOr(err, kErrBucket);
+    }
+}
+
+// Descriptor job i of a tile of TILE y: {first multiple, tl, p | w2 << 16,
+// first multiple of p^2 or kNone when p^2 > TILE}; *single = the one multiple
+// of p^2 in the tile when p^2 > TILE.  Jobs: the primes 11 <= p < 512 in
+// order (index 4 + i), largest work first.
+template <int TILE>
+__device__ __forceinline__ uint4 t2_desc(const T2Args &a, uint32_t i, uint32_t a0,
+                                         uint32_t tl, uint32_t *single)
+{
+    const uint32_t t = 4 + i, lo = 0, hi = tl;
+    *single = kNone;
+    const uint4 q = a.pq[t];
+    const uint32_t p = q.x;
+    const uint32_t v = a.r[t] + a0 + lo;  // < 2^31
+    const uint32_t rem = v - div_magic32(v, q.y, q.w & 255u) * p;
+    const uint32_t p2 = p * p;
+    const uint32_t v2 = (uint32_t)a.r2[t] + a0 + lo;  // < 2^31
+    const uint32_t rem2 = v2 - div_magic32(v2, q.z, (q.w >> 8) & 255u) * p2;
+    uint32_t s2 = lo + (rem2 ? p2 - rem2 : 0u);
+    if (p2 > (uint32_t)TILE) {
+        *single = s2 < hi ? s2 : kNone;
+        s2 = kNone;
+    }
+    return make_uint4(lo + (rem ? p - rem : 0u), hi, p | ((q.w >> 16) << 16), s2);
+}
+
+// Descriptor job: weights at the multiples of p in [first, hi), lanes over
+// them (the step 32p is a multiple of 4, so a lane's shifted weight is
+// loop-invariant; unrolled by hand, so no trip count is divided out), then
+// the square flags at the multiples of p^2.
+__device__ __forceinline__ void t2_desc_job(uint4 d, uint32_t *w, uint32_t lane)
+{
+    const uint32_t p = d.z & 0xffffu;
+    const uint32_t yo = d.x + lane * p;
+    if (yo < d.y) {
+        const uint32_t wsh = (d.z >> 16) << ((yo & 3u) << 3);
+        const uint32_t step = 8u * p;                      // words per 32 multiples
+        const uint32_t end = (d.y + 3u - (yo & 3u)) >> 2;  // yo' < hi  <=>  yo' >> 2 < end
+        uint32_t wi = yo >> 2;
+        for (; wi + 3u * step < end; wi += 4u * step) {
+            atomicAdd(&w[wi], wsh);
+            atomicAdd(&w[wi + step], wsh);
+            atomicAdd(&w[wi + 2u * step], wsh);
+            atomicAdd(&w[wi + 3u * step], wsh);
+        }
+        for (; wi < end; wi += step)
+            atomicAdd(&w[wi], wsh);
+    }
+    if (d.w != kNone) {
+        const uint32_t p2 = p * p;
+        for (uint32_t y2o = d.w + lane * p2; y2o < d.y; y2o += 32u * p2)
+            atomicOr(&w[y2o >> 2], 0x80u << ((y2o & 3u) << 3));
+    }
+}
+
+// One prime p >= 512 over the whole tile (one lane): its weights, and its
+// square when p < 8192 (p^2 > tile: at most one multiple).  Its per-block
+// record q = {p, m32(p), y1 mod p, s(p) | w2(p) << 8} and, below 8192,
+// e = {y1 mod p^2 | s(p^2) << 26, m32(p^2)} (see t2_block_prep_kernel).
+template <int TILE>
+__device__ __forceinline__ void t2_lane_prime(uint4 q, uint2 e, uint32_t *w, uint32_t a0,
+                                              uint32_t tl)
+{
+    const uint32_t p = q.x;
+    const uint32_t wt = q.w >> 8;
+    const uint32_t v = q.z + a0;  // < 2^31
+    const uint32_t rem = v - div_magic32(v, q.y, q.w & 255u) * p;
+    uint32_t yo = rem ? p - rem : 0u;
+    if (p < (uint32_t)TILE / 9u) {
+        // four hits per round: p is odd, so the four byte positions of
+        // yo, yo+p, yo+2p, yo+3p repeat every 4p
+        const uint32_t w0 = wt << ((yo & 3u) << 3);
+        const uint32_t w1 = wt << (((yo + p) & 3u) << 3);
+        const uint32_t w2 = wt << (((yo + 2u * p) & 3u) << 3);
+        const uint32_t w3 = wt << (((yo + 3u * p) & 3u) << 3);
+        for (; yo + 3u * p < tl; yo += 4u * p) {
+            atomicAdd(&w[yo >> 2], w0);
+            atomicAdd(&w[(yo + p) >> 2], w1);
+            atomicAdd(&w[(yo + 2u * p) >> 2], w2);
+            atomicAdd(&w[(yo + 3u * p) >> 2], w3);
+        }
+        if (yo < tl) {
+            atomicAdd(&w[yo >> 2], w0);
+            if (yo + p < tl) {
+                atomicAdd(&w[(yo + p) >> 2], w1);
+                if (yo + 2u * p < tl)
+                    atomicAdd(&w[(yo + 2u * p) >> 2], w2);
+            }
+        }
+    } else if (p < (uint32_t)TILE) {
+        for (; yo < tl; yo += p)
+            atomicAdd(&w[yo >> 2], __funnelshift_l(0u, wt, yo << 3));
+    } else if (yo < tl) {
+        atomicAdd(&w[yo >> 2], __funnelshift_l(0u, wt, yo << 3));  // at most one multiple
+    }
+    if (p < kT2ListMin) {
+        // p^2 < 2^26: the first multiple of p^2 at or after the tile start;
+        // e.y = m32(p^2), its shift below 32 in the low bits of e.x's spare
+        // room is not needed: y1 mod p^2 < 2^26 leaves e.x bits 26..31 for it
+        const uint32_t p2 = p * p;
+        const uint32_t v2 = (e.x & 0x3ffffffu) + a0;  // < 2^31
+        const uint32_t rem2 = v2 - div_magic32(v2, e.y, e.x >> 26) * p2;
+        const uint32_t o2 = rem2 ? p2 - rem2 : 0u;
+        if (o2 < tl)
+            atomicOr(&w[o2 >> 2], 0x80u << ((o2 & 3u) << 3));
+    }
+}
+
+// mu of four y (one word of the tile) as the prefix word
+//     D = byte j: 4 + sum of mu over bytes 0..j,
+// from the square flags (bit 7 of each byte) and, with a tile threshold, the
+// biased bytes W = (byte & 127) + bias: with nsq = 1 where no square divides
+// and m = 1 where mu = -1 (nsq and bit 0 xor bit 7 of W), mu + 1 = 1 + nsq -
+// 2m per byte, so D = (nsq - 2m) 0x01010101 + 0x04040404 (mod 2^32).  keep
+// masks the bytes past the tile's end (mu = 0 there).
+__device__ __forceinline__ uint32_t t2_word(uint32_t ws, uint32_t bias4, uint32_t keep,
+                                            bool tile_thr, uint64_t y0, float thr_half,
+                                            uint32_t *nsq_out, uint32_t *m_out)
+{
+    const uint32_t nsq = ~(ws >> 7) & 0x01010101u & keep;
+    uint32_t m;
+    if (tile_thr) {
+        const uint32_t W = (ws & 0x7f7f7f7fu) + bias4;
+        m = (W ^ (W >> 7)) & nsq;
+    } else {
+        m = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int A = (int)((ws >> (8 * j)) & 127u) - 1;
+            const int th = (int)floorf(2.0f * __log2f(__ull2float_rn(y0 + j)) - thr_half);
+            // count parity xor [c > 1]
+            const uint32_t bit = ((uint32_t)A & 1u) ^ (A > th ? 0u : 1u);
+            m |= bit << (8 * j);
+        }
+        m &= nsq;
+    }
+    *nsq_out = nsq;
+    *m_out = m;
+    return (nsq - 2u * m) * 0x01010101u + 0x04040404u;
+}
+
+// Decode + scan of one scale-2 tile: each warp owns two 2048-y segments; a
+// round covers 1024 y, each lane 16 y at 16 lane and 16 y at 512 + 16 lane
+// (16-byte shared loads without bank conflicts), and one warp scan carries
+// both halves' lane sums packed in one int32 (low and high 16-bit fields;
+// every partial sum is within +-512).
+__device__ __forceinline__ void t2_tile_decode(const T2Args &a, const uint4 *sb, uint32_t a0,
+                                               uint64_t t1, uint32_t tl, uint32_t lane,
+                                               uint32_t warp)
+{
+    const bool tile_thr = t1 >= kByteTileThrMin;
+    uint32_t bias4 = 0;
+    if (tile_thr) {
+        int thr = (int)floorf(2.0f * log2f(__ull2float_rn(t1)) - a.thr_half);
+        thr &= ~1;
+        bias4 = (uint32_t)(126 - thr) * 0x01010101u;
+    }
+    for (uint32_t sgi = 0; sgi < 2; ++sgi) {
+        const uint32_t so = warp * (2u * kSegY) + sgi * kSegY;  // segment start in the tile
+        if (so >= tl)
+            break;
+        const uint64_t ys = t1 + so;
+        const bool want_mu = a.mu_out && ys <= a.mu_end && ys + (kSegY - 1) >= a.mu_base;
+        int run = 0;
+#pragma unroll 1
+        for (uint32_t r = 0; r < (uint32_t)kSegY / 1024u; ++r) {
+            uint32_t D[8];
+            int tot[2] = {0, 0};
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t o0 = so + r * 1024u + (uint32_t)h * 512u + lane * 16u;
+                const uint4 q4 = sb[o0 >> 4];
+                const uint32_t ws[4] = {q4.x, q4.y, q4.z, q4.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const uint32_t ok = o0 + 4u * k;
+                    const uint32_t keep = ok + 4u <= tl ? 0xffffffffu
+                                          : (ok >= tl ? 0u : 0xffffffffu >> (8u * (ok + 4u - tl)));
+                    uint32_t nsq, m;
+                    D[4 * h + k] = t2_word(ws[k], bias4, keep, tile_thr, t1 + ok, a.thr_half,
+                                           &nsq, &m);
+                    tot[h] += (int)(D[4 * h + k] >> 24) - 4;
+                    if (want_mu) {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const uint64_t y = t1 + ok + j;
+                            const int mu = (int)((nsq >> (8 * j)) & 1u) -
+                                           2 * (int)((m >> (8 * j)) & 1u);
+                            if (ok + j < tl && y >= a.mu_base && y <= a.mu_end)
+                                a.mu_out[y - a.mu_base] = (int8_t)mu;
+                        }
+                    }
+                }
+            }
+            // packed inclusive scan of (tot[0], tot[1]) over the lanes
+            int inc = tot[0] + tot[1] * 65536;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int nb = __shfl_up_sync(0xffffffffu, inc, o);
+                if ((int)lane >= o)
+                    inc += nb;
+            }
+            const int all = __shfl_sync(0xffffffffu, inc, 31);
+            const int incA = (int)(int16_t)(inc & 0xffff), incB = (inc - incA) >> 16;
+            const int allA = (int)(int16_t)(all & 0xffff), allB = (all - allA) >> 16;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t o0 = so + r * 1024u + (uint32_t)h * 512u + lane * 16u;
+                // M relative to the segment, before the lane's 16 y
+                int rb = run + (h == 0 ? incA - tot[0] : allA + incB - tot[1]);
+                uint32_t out[8];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const uint32_t Dk = D[4 * h + k];
+                    // halfword = 0x8000 + value, so no borrow crosses halves; the
+                    // xor turns 0x8000 + v into v mod 2^16
+                    const uint32_t bx = (uint32_t)(rb - 4) * 0x00010001u;
+                    out[2 * k] = (bx + __byte_perm(Dk, 0x80u, 0x4140)) ^ 0x80008000u;
+                    out[2 * k + 1] = (bx + __byte_perm(Dk, 0x80u, 0x4342)) ^ 0x80008000u;
+                    rb += (int)(Dk >> 24) - 4;
+                }
+                int16_t *dst = a.Mloc + a0 + o0;
+                if (o0 + 16u <= tl) {
+                    reinterpret_cast<uint4 *>(dst)[0] = make_uint4(out[0], out[1], out[2], out[3]);
+                    reinterpret_cast<uint4 *>(dst)[1] = make_uint4(out[4], out[5], out[6], out[7]);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 16; ++k)
+                        if (o0 + k < tl)
+                            dst[k] = (int16_t)(out[k >> 1] >> (16 * (k & 1)));
+                }
+            }
+            run += allA + allB;
+        }
+        if (lane == 0)
+            a.segsum[(a0 + so) >> kSegShift] = run;
+    }
+}
+
+template <int TILE, int THREADS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) mu_sieve_t2_kernel(T2Args a)
+{
+    static_assert(TILE == THREADS * 128, "each warp decodes two 2048-y segments");
+    static_assert(THREADS >= (int)kT2JobsMax, "one descriptor per thread");
+    extern __shared__ uint4 sb[];
+    uint32_t *w = reinterpret_cast<uint32_t *>(sb);  // TILE / 4 words, four y each
+    __shared__ uint32_t s_job;
+    __shared__ uint4 s_jd[kT2JobsMax];
+    __shared__ uint64_t s_mbar;
+    const uint32_t a0 = blockIdx.x * (uint32_t)TILE;
+    const uint64_t t1 = a.y1 + a0;
+    const uint32_t tl = min(a.len - a0, (uint32_t)TILE);
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t jd = a.np_lane - 4;  // descriptor jobs: primes 11 <= p < 512
+    const uint32_t jobs = jd + (a.np - a.np_lane + 63u) / 64u;
+    const uint32_t nsq = min(a.sqcnt[blockIdx.x], a.sqcap);
+
+    uint32_t single = kNone;
+    {
+        // the tile's bytes: one bulk asynchronous copy of the first pattern's
+        // phase, overlapped with the job descriptors
+        const uint32_t ph = (uint32_t)(t1 % kPatternPeriod);
+        if (threadIdx.x == 0) {
+            mbar_init(&s_mbar);
+            fence_proxy_async_smem();
+            mbar_arrive_expect(&s_mbar, (uint32_t)TILE + a.extra_tx);
+            bulk_copy_g2s(sb, a.pat + (size_t)(ph & 15u) * (kPat2Len / 16) + (ph >> 4),
+                          (uint32_t)TILE, &s_mbar);
+            s_job = 0;
+        }
+        if (threadIdx.x < jd)
+            s_jd[threadIdx.x] = t2_desc<TILE>(a, threadIdx.x, a0, tl, &single);
+    }
+    __syncthreads();  // the mbarrier is initialised; every thread has read sqcnt
+    if (__syncthreads_or(!mbar_wait(&s_mbar, 0u))) {
+        // the copy did not land in time: flag it, give it one more bounded
+        // wait (it writes this CTA's shared memory), and leave the tile
+        if (threadIdx.x == 0) {
+            a.sqcnt[blockIdx.x] = 0;
+            if (a.err)
+                atomicOr(a.err, kErrTimeout);
+        }
+        mbar_wait(&s_mbar, 0u);
+        return;
+    }
+    if (threadIdx.x == 0)
+        a.sqcnt[blockIdx.x] = 0;  // read above; cleared for the next block
+    if (single != kNone)
+        atomicOr(&w[single >> 2], 0x80u << ((single & 3u) << 3));
+    {
+        const uint32_t *ls = a.sqlist + (size_t)blockIdx.x * a.sqcap;
+        for (uint32_t i = threadIdx.x; i < nsq; i += THREADS) {
+            const uint32_t o = ls[i];
+            atomicOr(&w[o >> 2], 0x80u << ((o & 3u) << 3));
+        }
+    }
+
+    // jobs, largest first, handed out through a shared counter: descriptor
+    // jobs (a warp over the multiples of one prime), then 64 primes >= 512 at
+    // a time (a lane takes primes i and 63 - i of the job, so the lanes' hit
+    // counts even out)
+    for (;;) {
+        uint32_t job = 0;
+        if (lane == 0)
+            job = atomicAdd(&s_job, 1u);
+        job = __shfl_sync(0xffffffffu, job, 0);
+        if (job >= jobs)
+            break;
+        if (job < jd) {
+            t2_desc_job(s_jd[job], w, lane);
+        } else {
+            const uint32_t b0 = a.np_lane + (job - jd) * 64u;
+            const uint32_t t0 = b0 + lane, t1p = b0 + 63u - lane;
+            uint4 q0 = make_uint4(0, 0, 0, 0), q1 = q0;
+            uint2 e0 = make_uint2(0, 0), e1 = e0;
+            if (t0 < a.np) {
+                q0 = a.rec[t0];
+                if (t0 < a.np_list)
+                    e0 = a.rec2[t0];
+            }
+            if (t1p < a.np) {
+                q1 = a.rec[t1p];
+                if (t1p < a.np_list)
+                    e1 = a.rec2[t1p];
+            }
+            if (t0 < a.np)
+                t2_lane_prime<TILE>(q0, e0, w, a0, tl);
+            if (t1p < a.np)
+                t2_lane_prime<TILE>(q1, e1, w, a0, tl);
+        }
+    }
+    __syncthreads();
+
+    t2_tile_decode(a, sb, a0, t1, tl, lane, warp);
+}
+
+// ---------------------------------------------------------------------------
 // a1 + a2, persistent byte variant for blocks with many large primes.  One
 // CTA per SM takes a contiguous range of tiles of the block and keeps, across
 // its tiles:
@@ -634,7 +1066,6 @@ __global__ void __launch_bounds__(kSieveThreads, 1) mu_sieve_byte_kernel(ByteArg
 constexpr uint32_t kMedMax = 12288;          // primes in [2048, 2^17): 11942
 constexpr uint32_t kPersistTilesMax = 128;   // tiles per CTA (blocks <= 2^30 y, >= 64 CTAs)
 constexpr uint32_t kBucketJob = 256;         // bucket entries per job (8 per lane)
-constexpr uint32_t kErrBucket = 4u;
 
 __device__ __forceinline__ uint64_t bucket_entry(uint32_t p, uint32_t w, uint32_t off)
 {
@@ -935,6 +1366,39 @@ static const BytePatterns &byte_patterns(uint32_t S)
     return bp;
 }
 
+// Host copy of the scale-2 byte pattern (see mu_sieve_t2_kernel), 16 phase
+// copies (copy k starts at phase k), built once per process: 1 + the weights
+// of 2, 3, 5, 7, plus 128 where 4, 9, 25 or 49 divides (period 44100).
+struct T2Patterns {
+    std::vector<uint8_t> a;
+};
+
+static const T2Patterns &t2_patterns()
+{
+    static std::mutex mu;
+    static T2Patterns tp;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!tp.a.empty())
+        return tp;
+    const uint32_t small[4] = {2, 3, 5, 7};
+    std::vector<uint8_t> pat(kPatternPeriod);
+    for (uint32_t i = 0; i < kPatternPeriod; ++i) {
+        uint32_t b = 1;
+        for (int q = 0; q < 4; ++q) {
+            if (i % small[q] == 0)
+                b += byte_weight(small[q], 2);
+            if (i % (small[q] * small[q]) == 0)
+                b |= 128u;
+        }
+        pat[i] = (uint8_t)b;
+    }
+    tp.a.resize((size_t)16 * kPat2Len);
+    for (uint32_t k = 0; k < 16; ++k)
+        for (uint32_t j = 0; j < kPat2Len; ++j)
+            tp.a[(size_t)k * kPat2Len + j] = pat[(k + j) % kPatternPeriod];
+    return tp;
+}
+
 // Tables of the byte sieve (see mu_sieve_byte_kernel).
 static int byte_tables_create(PrimeTable *t, const std::vector<uint32_t> &pr, cudaStream_t s)
 {
@@ -972,6 +1436,18 @@ static int byte_tables_create(PrimeTable *t, const std::vector<uint32_t> &pr, cu
     cudaMemcpyAsync(t->pq, pq.data(), np * sizeof(uint4), cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(t->pat8, p8.data(), p8.size(), cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(t->patsq, psq.data(), kPatSqWords * 4, cudaMemcpyHostToDevice, s);
+    // scale-2 records: the same constants with w2(p) in place of w(p)
+    for (size_t i = 0; i < np; ++i)
+        pq[i].w = (pq[i].w & 0xffffu) | (byte_weight(pr[i], 2) << 16);
+    const T2Patterns &tp = t2_patterns();
+    t->pq2 = (uint4 *)dev_alloc(t->al, np * sizeof(uint4));
+    t->pat2 = (uint4 *)dev_alloc(t->al, tp.a.size());
+    t->rec = (uint4 *)dev_alloc(t->al, np * sizeof(uint4));
+    t->rec2 = (uint2 *)dev_alloc(t->al, np * sizeof(uint2));
+    if (!t->pq2 || !t->pat2 || !t->rec || !t->rec2)
+        return 2;
+    cudaMemcpyAsync(t->pq2, pq.data(), np * sizeof(uint4), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(t->pat2, tp.a.data(), tp.a.size(), cudaMemcpyHostToDevice, s);
     if (cudaStreamSynchronize(s) != cudaSuccess)
         return 3;
     return 0;
@@ -1062,6 +1538,10 @@ void prime_table_destroy(PrimeTable *t)
     dev_free(t->al, t->blk_r2, np * 8);
     dev_free(t->al, t->pat8, (size_t)16 * kPat8Len);
     dev_free(t->al, t->patsq, kPatSqWords * 4);
+    dev_free(t->al, t->pq2, np * sizeof(uint4));
+    dev_free(t->al, t->pat2, (size_t)16 * kPat2Len);
+    dev_free(t->al, t->rec, np * sizeof(uint4));
+    dev_free(t->al, t->rec2, np * sizeof(uint2));
     if (t->pw)
         dev_free(t->al, t->pw, ((size_t)t->np_mid + 1) * 4);
     if (t->scratch_len) {
@@ -1069,6 +1549,9 @@ void prime_table_destroy(PrimeTable *t)
         dev_free(t->al, t->bucket, ntiles * t->bucket_cap * 8);
         dev_free(t->al, t->gsq, ntiles * (kByteTile / 8));
         dev_free(t->al, t->perr, 4);
+        const uint64_t nt2 = (t->scratch_len + kT2MinTile - 1) / kT2MinTile;
+        dev_free(t->al, t->sqcnt, nt2 * 4);
+        dev_free(t->al, t->sqlist, nt2 * t->sq_cap * 4);
     }
     free(t->host_p);
     *t = PrimeTable();
@@ -1110,6 +1593,23 @@ int sieve_scratch_create(PrimeTable *t, uint64_t max_len)
         t->gsq = nullptr;
         t->perr = nullptr;
         return 2;
+    }
+    // square lists of the scale-2 kernel: the primes 8192 <= q <= P put about
+    // T / (8192 ln 8192) multiples of q^2 into a tile of T y (1.3 for 96 Ki
+    // y); the kernel clears its tile's count after reading it, so the counts
+    // start at zero once, here
+    const uint64_t nt2 = (max_len + kT2MinTile - 1) / kT2MinTile;
+    t->sq_cap = 64;
+    t->sqcnt = (uint32_t *)dev_alloc(t->al, nt2 * 4);
+    t->sqlist = (uint32_t *)dev_alloc(t->al, nt2 * t->sq_cap * 4);
+    if (!t->sqcnt || !t->sqlist) {
+        dev_free(t->al, t->sqcnt, nt2 * 4);
+        dev_free(t->al, t->sqlist, nt2 * t->sq_cap * 4);
+        t->sqcnt = nullptr;
+        t->sqlist = nullptr;
+        t->sq_cap = 0;
+    } else {
+        cudaMemset(t->sqcnt, 0, nt2 * 4);
     }
     cudaMemset(t->perr, 0, 4);
     t->bucket_cap = cap;
@@ -1158,6 +1658,65 @@ static bool byte_path_ok(const PrimeTable *t, uint64_t y2, uint64_t P, uint64_t 
     return half >= E + 2.5 && thr < 126.0 && 127.0 + half + E + 3.0 < 255.0;
 }
 
+// The scale-2 kernel is exact when log2 P - E >= 2.5 (E as above); it also
+// needs the biased bytes below 2^8 (1 + A + 126 - thr, A <= 2 log2 y2 + E),
+// the sums below 2^7 (bit 7 is the square flag), thr < 126, P >= 2^10 and
+// blocks of at most 2^30 y; and its scratch (square lists, status word).
+static bool t2_path_ok(const PrimeTable *t, uint64_t y2, uint64_t P, uint64_t len)
+{
+    if (!t->pq2 || !t->sqcnt || !t->perr || P < 1024 || y2 >= (1ull << 54) ||
+        len > (1ull << 30) || len > t->scratch_len)
+        return false;
+    const double half = std::log2((double)P);
+    const int E = omega_max(y2);
+    const double thr = 2.0 * std::log2((double)y2) - half;
+    const double amax = 2.0 * std::log2((double)y2) + E;
+    return half >= E + 2.5 && thr < 124.0 && 1.0 + amax < 127.0 &&
+           amax - (thr - 2.0) + 127.0 < 255.0;
+}
+
+template <int TILE, int THREADS, int MINB>
+static int t2_launch(const PrimeTable *t, const SieveLaunch &L, uint32_t np, uint64_t P,
+                     cudaStream_t s)
+{
+    static std::atomic<uint64_t> attr_devs{0};
+    const uint64_t dbit = device_bit();
+    if (attrs_needed(attr_devs, dbit)) {
+        cudaFuncSetAttribute(mu_sieve_t2_kernel<TILE, THREADS, MINB>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, TILE);
+        attrs_done(attr_devs, dbit);
+    }
+    const uint32_t tiles = (uint32_t)((L.len + TILE - 1) / TILE);
+    T2Args a{};
+    a.y1 = L.y1;
+    a.len = (uint32_t)L.len;
+    a.np = np;
+    a.np_lane = std::min(prime_count_upto(t, kT2LaneMin - 1), np);
+    a.np_list = std::min(prime_count_upto(t, kT2ListMin - 1), np);
+    a.thr_half = (float)std::log2((double)P);
+    a.pq = t->pq2;
+    a.r = t->blk_r;
+    a.r2 = t->blk_r2;
+    a.rec = t->rec;
+    a.rec2 = t->rec2;
+    a.pat = t->pat2;
+    a.sqcnt = t->sqcnt;
+    a.sqlist = t->sqlist;
+    a.sqcap = t->sq_cap;
+    a.Mloc = L.Mloc;
+    a.segsum = L.segsum;
+    a.mu_out = L.mu_out;
+    a.mu_base = L.mu_base;
+    a.mu_end = L.mu_end;
+    a.err = t->perr;
+    a.extra_tx = getenv("MERTENS_TEST_STALL_COPY") ? 16u : 0u;
+    t2_block_prep_kernel<<<(np + 255) / 256, 256, 0, s>>>(
+        L.y1, np, t->pq2, t->blk_r, t->blk_r2, a.np_lane, t->rec, t->rec2, a.np_list, a.len,
+        (uint32_t)TILE, t->sqcnt, t->sqlist, t->sq_cap, t->perr);
+    mu_sieve_t2_kernel<TILE, THREADS, MINB><<<tiles, THREADS, TILE, s>>>(a);
+    return 2;
+}
+
 int sieve_block_enqueue(const PrimeTable *t, const SieveLaunch &L, cudaStream_t s)
 {
     static std::atomic<uint64_t> attr_devs{0};
@@ -1179,6 +1738,34 @@ int sieve_block_enqueue(const PrimeTable *t, const SieveLaunch &L, cudaStream_t 
     const uint32_t np_small = prime_count_upto(t, 2047);
     const bool bytes = byte_path_ok(t, y2, P, L.len) && getenv("MERTENS_SIEVE16") == nullptr;
     int launches = 0;
+    // the scale-2 kernel where it is exact and the bucketed kernel does not
+    // pay (MERTENS_SIEVE_BYTE4 / MERTENS_SIEVE_TILES keep the scale-4/3 per-tile
+    // kernel, MERTENS_SIEVE_BUCKETS the bucketed one, MERTENS_SIEVE16 the
+    // 16-bit one; MERTENS_T2_TILE=64 takes 64 Ki-y tiles)
+    {
+        const uint32_t nmid = std::min(t->np_mid, np);
+        const bool persist = bytes && t->bucket && L.len <= t->scratch_len && np_small < np &&
+                             (np - nmid > 3u * (nmid - std::min(np_small, nmid)) ||
+                              getenv("MERTENS_SIEVE_BUCKETS") != nullptr) &&
+                             getenv("MERTENS_SIEVE_TILES") == nullptr;
+        const bool t2 = bytes && !persist && t2_path_ok(t, y2, P, L.len) &&
+                        getenv("MERTENS_SIEVE_BYTE4") == nullptr &&
+                        getenv("MERTENS_SIEVE_TILES") == nullptr;
+        if (t2) {
+            const char *tt = getenv("MERTENS_T2_TILE");
+            launches += (tt && tt[0] == '6') ? t2_launch<65536, 512, 3>(t, L, np, P, s)
+                                             : t2_launch<98304, 768, 2>(t, L, np, P, s);
+            if (L.mid)
+                cudaEventRecord(L.mid, s);
+            if (L.mid2)
+                cudaEventRecord(L.mid2, s);
+            const uint32_t nseg = (uint32_t)sieve_segments(L.len);
+            seg_carry_kernel<<<(nseg + 1023) / 1024, 1024, 0, s>>>(L.segsum, nseg, L.carry_in,
+                                                                  L.segoff, L.carry_out);
+            ++launches;
+            return cudaGetLastError() == cudaSuccess ? launches : -1;
+        }
+    }
     if (np > 4) {
         sieve_block_prep_kernel<<<(np + 255) / 256, 256, 0, s>>>(
             L.y1, np, t->p, t->blk_r, t->blk_qm, bytes ? t->blk_r2 : nullptr);

@@ -90,26 +90,31 @@ def test_sieve_M_with_carry_far_from_one():
 
 @pytest.mark.parametrize("y1,length", [
     (1, 3 * 10**6 + 11),
+    (2**26 - 5 * 65536 + 77, 11 * 65536 + 3),    # per-y thresholds, then per tile
     (7 * 10**9 + 1, 4 * BYTE_TILE + 999),
+    (4 * 10**10 - (1 << 24), 1 << 24),           # the top of the n = 10^16 sieve range
     (3 * 10**11 + 17, 300 * BYTE_TILE + 5),      # primes above 2^17: bucketed
     (2**45 + 3, 70 * BYTE_TILE + 1),             # weight scale 3, 5.9e6 sieving primes
 ])
 def test_sieve_kernels_agree(y1, length, monkeypatch):
-    """The persistent bucketed byte kernel, the per-tile byte kernel and the
-    16-bit kernel (each forced by its switch) give the same M(y), and match the
-    oracle's mu."""
+    """The default kernel (scale-2 bytes with 96 Ki-y tiles where it is exact),
+    its 64 Ki-y variant, the persistent bucketed byte kernel, the per-tile
+    scale-4/3 byte kernel and the 16-bit kernel (each forced by its switch)
+    give the same M(y), and match the oracle's mu."""
     # the carry only shifts every M(y); far out it is left at 0
     carry = 0 if y1 == 1 or y1 > 10**12 else oracle.mertens(y1 - 1, L=10**7)
     out = []
-    for env in ("MERTENS_SIEVE_BUCKETS", "MERTENS_SIEVE_TILES", "MERTENS_SIEVE16"):
+    for env, val in ((None, None), ("MERTENS_T2_TILE", "64"), ("MERTENS_SIEVE_BUCKETS", "1"),
+                     ("MERTENS_SIEVE_TILES", "1"), ("MERTENS_SIEVE16", "1")):
         if env:
-            monkeypatch.setenv(env, "1")
+            monkeypatch.setenv(env, val)
         M = torch.empty(length, dtype=torch.int32, device="cuda")
         pm.mertens_sieve_M(y1, length, carry, M)
         out.append(M.cpu().numpy())
         if env:
             monkeypatch.delenv(env)
-    assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
+    for i in range(1, len(out)):
+        assert np.array_equal(out[0], out[i]), i
     ref = carry + np.cumsum(oracle.mu_window(y1, length).astype(np.int64))
     assert np.array_equal(out[0].astype(np.int64), ref)
 
