@@ -853,11 +853,118 @@ __device__ __forceinline__ uint32_t t2_word(uint32_t ws, uint32_t bias4, uint32_
     return (nsq - 2u * m) * 0x01010101u + 0x04040404u;
 }
 
-// Decode + scan of one scale-2 tile: each warp owns two 2048-y segments; a
-// round covers 1024 y, each lane 16 y at 16 lane and 16 y at 512 + 16 lane
-// (16-byte shared loads without bank conflicts), and one warp scan carries
-// both halves' lane sums packed in one int32 (low and high 16-bit fields;
-// every partial sum is within +-512).
+// Decode + scan of one 2048-y segment of a scale-2 tile (one warp): a round
+// covers 1024 y, each lane 16 y at 16 lane and 16 y at 512 + 16 lane (16-byte
+// shared loads without bank conflicts), and one warp scan carries both
+// halves' lane sums packed in one int32 (low and high 16-bit fields; every
+// partial sum is within +-512).  kFast: the segment is whole, the tile takes
+// one threshold and no mu is written, so none of the checks for those cases
+// is issued.  Returns the segment's mu sum.
+template <bool kFast>
+__device__ int t2_segment(const T2Args &a, const uint4 *sb, uint32_t a0,
+                          uint64_t t1, uint32_t tl, uint32_t so, uint32_t lane, uint32_t bias4,
+                          bool tile_thr, bool want_mu)
+{
+    int run = 0;
+#pragma unroll 1
+    for (uint32_t r = 0; r < (uint32_t)kSegY / 1024u; ++r) {
+        uint32_t D[8];
+        int tot[2] = {0, 0};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t o0 = so + r * 1024u + (uint32_t)h * 512u + lane * 16u;
+            const uint4 q4 = sb[o0 >> 4];
+            const uint32_t ws[4] = {q4.x, q4.y, q4.z, q4.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t ok = o0 + 4u * k;
+                uint32_t nsq, m;
+                if (kFast) {
+                    nsq = ~(ws[k] >> 7) & 0x01010101u;
+                    const uint32_t W = (ws[k] & 0x7f7f7f7fu) + bias4;
+                    m = (W ^ (W >> 7)) & nsq;
+                    D[4 * h + k] = (nsq - 2u * m) * 0x01010101u + 0x04040404u;
+                } else {
+                    const uint32_t keep =
+                        ok + 4u <= tl ? 0xffffffffu
+                                      : (ok >= tl ? 0u : 0xffffffffu >> (8u * (ok + 4u - tl)));
+                    D[4 * h + k] = t2_word(ws[k], bias4, keep, tile_thr, t1 + ok, a.thr_half,
+                                           &nsq, &m);
+                    if (want_mu) {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const uint64_t y = t1 + ok + j;
+                            const int mu = (int)((nsq >> (8 * j)) & 1u) -
+                                           2 * (int)((m >> (8 * j)) & 1u);
+                            if (ok + j < tl && y >= a.mu_base && y <= a.mu_end)
+                                a.mu_out[y - a.mu_base] = (int8_t)mu;
+                        }
+                    }
+                }
+                tot[h] += (int)(D[4 * h + k] >> 24) - 4;
+            }
+        }
+        // packed inclusive scan of (tot[0], tot[1]) over the lanes
+        int inc = tot[0] + tot[1] * 65536;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int nb = __shfl_up_sync(0xffffffffu, inc, o);
+            if ((int)lane >= o)
+                inc += nb;
+        }
+        const int all = __shfl_sync(0xffffffffu, inc, 31);
+        const int incA = (int)(int16_t)(inc & 0xffff), incB = (inc - incA) >> 16;
+        const int allA = (int)(int16_t)(all & 0xffff), allB = (all - allA) >> 16;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t o0 = so + r * 1024u + (uint32_t)h * 512u + lane * 16u;
+            // M relative to the segment, before the lane's 16 y
+            int rb = run + (h == 0 ? incA - tot[0] : allA + incB - tot[1]);
+            uint32_t out[8];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t Dk = D[4 * h + k];
+                // halfword = 0x8000 + value, so no borrow crosses halves; the
+                // xor turns 0x8000 + v into v mod 2^16
+                const uint32_t bx = (uint32_t)(rb - 4) * 0x00010001u;
+                out[2 * k] = (bx + __byte_perm(Dk, 0x80u, 0x4140)) ^ 0x80008000u;
+                out[2 * k + 1] = (bx + __byte_perm(Dk, 0x80u, 0x4342)) ^ 0x80008000u;
+                rb += (int)(Dk >> 24) - 4;
+            }
+            int16_t *dst = a.Mloc + a0 + o0;
+            if (kFast || o0 + 16u <= tl) {
+                reinterpret_cast<uint4 *>(dst)[0] = make_uint4(out[0], out[1], out[2], out[3]);
+                reinterpret_cast<uint4 *>(dst)[1] = make_uint4(out[4], out[5], out[6], out[7]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 16; ++k)
+                    if (o0 + k < tl)
+                        dst[k] = (int16_t)(out[k >> 1] >> (16 * (k & 1)));
+            }
+        }
+        run += allA + allB;
+    }
+    return run;
+}
+
+__device__ __forceinline__ int t2_segment_fast(const T2Args &a, const uint4 *sb, uint32_t a0,
+                                               uint64_t t1, uint32_t tl, uint32_t so,
+                                               uint32_t lane, uint32_t bias4)
+{
+    return t2_segment<true>(a, sb, a0, t1, tl, so, lane, bias4, true, false);
+}
+
+// The rare segments (a ragged end, thresholds per y, mu written) in a
+// function of their own, so they hold no registers of the common path.
+__device__ __noinline__ int t2_segment_general(const T2Args &a, const uint4 *sb, uint32_t a0,
+                                               uint64_t t1, uint32_t tl, uint32_t so,
+                                               uint32_t lane, uint32_t bias4, bool tile_thr,
+                                               bool want_mu)
+{
+    return t2_segment<false>(a, sb, a0, t1, tl, so, lane, bias4, tile_thr, want_mu);
+}
+
+// Decode + scan of one scale-2 tile: each warp owns two 2048-y segments.
 __device__ __forceinline__ void t2_tile_decode(const T2Args &a, const uint4 *sb, uint32_t a0,
                                                uint64_t t1, uint32_t tl, uint32_t lane,
                                                uint32_t warp)
@@ -875,77 +982,10 @@ __device__ __forceinline__ void t2_tile_decode(const T2Args &a, const uint4 *sb,
             break;
         const uint64_t ys = t1 + so;
         const bool want_mu = a.mu_out && ys <= a.mu_end && ys + (kSegY - 1) >= a.mu_base;
-        int run = 0;
-#pragma unroll 1
-        for (uint32_t r = 0; r < (uint32_t)kSegY / 1024u; ++r) {
-            uint32_t D[8];
-            int tot[2] = {0, 0};
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const uint32_t o0 = so + r * 1024u + (uint32_t)h * 512u + lane * 16u;
-                const uint4 q4 = sb[o0 >> 4];
-                const uint32_t ws[4] = {q4.x, q4.y, q4.z, q4.w};
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const uint32_t ok = o0 + 4u * k;
-                    const uint32_t keep = ok + 4u <= tl ? 0xffffffffu
-                                          : (ok >= tl ? 0u : 0xffffffffu >> (8u * (ok + 4u - tl)));
-                    uint32_t nsq, m;
-                    D[4 * h + k] = t2_word(ws[k], bias4, keep, tile_thr, t1 + ok, a.thr_half,
-                                           &nsq, &m);
-                    tot[h] += (int)(D[4 * h + k] >> 24) - 4;
-                    if (want_mu) {
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            const uint64_t y = t1 + ok + j;
-                            const int mu = (int)((nsq >> (8 * j)) & 1u) -
-                                           2 * (int)((m >> (8 * j)) & 1u);
-                            if (ok + j < tl && y >= a.mu_base && y <= a.mu_end)
-                                a.mu_out[y - a.mu_base] = (int8_t)mu;
-                        }
-                    }
-                }
-            }
-            // packed inclusive scan of (tot[0], tot[1]) over the lanes
-            int inc = tot[0] + tot[1] * 65536;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int nb = __shfl_up_sync(0xffffffffu, inc, o);
-                if ((int)lane >= o)
-                    inc += nb;
-            }
-            const int all = __shfl_sync(0xffffffffu, inc, 31);
-            const int incA = (int)(int16_t)(inc & 0xffff), incB = (inc - incA) >> 16;
-            const int allA = (int)(int16_t)(all & 0xffff), allB = (all - allA) >> 16;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const uint32_t o0 = so + r * 1024u + (uint32_t)h * 512u + lane * 16u;
-                // M relative to the segment, before the lane's 16 y
-                int rb = run + (h == 0 ? incA - tot[0] : allA + incB - tot[1]);
-                uint32_t out[8];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const uint32_t Dk = D[4 * h + k];
-                    // halfword = 0x8000 + value, so no borrow crosses halves; the
-                    // xor turns 0x8000 + v into v mod 2^16
-                    const uint32_t bx = (uint32_t)(rb - 4) * 0x00010001u;
-                    out[2 * k] = (bx + __byte_perm(Dk, 0x80u, 0x4140)) ^ 0x80008000u;
-                    out[2 * k + 1] = (bx + __byte_perm(Dk, 0x80u, 0x4342)) ^ 0x80008000u;
-                    rb += (int)(Dk >> 24) - 4;
-                }
-                int16_t *dst = a.Mloc + a0 + o0;
-                if (o0 + 16u <= tl) {
-                    reinterpret_cast<uint4 *>(dst)[0] = make_uint4(out[0], out[1], out[2], out[3]);
-                    reinterpret_cast<uint4 *>(dst)[1] = make_uint4(out[4], out[5], out[6], out[7]);
-                } else {
-#pragma unroll
-                    for (int k = 0; k < 16; ++k)
-                        if (o0 + k < tl)
-                            dst[k] = (int16_t)(out[k >> 1] >> (16 * (k & 1)));
-                }
-            }
-            run += allA + allB;
-        }
+        const int run = (tile_thr && !want_mu && so + kSegY <= tl)
+                            ? t2_segment_fast(a, sb, a0, t1, tl, so, lane, bias4)
+                            : t2_segment_general(a, sb, a0, t1, tl, so, lane, bias4, tile_thr,
+                                                 want_mu);
         if (lane == 0)
             a.segsum[(a0 + so) >> kSegShift] = run;
     }

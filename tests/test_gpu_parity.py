@@ -126,6 +126,9 @@ def test_bounded_copy_wait_reports_timeout_and_device_stays_usable(monkeypatch):
     the same device is correct."""
     y1, length = 2**30 + 1, BYTE_TILE + 100
     M = torch.empty(length, dtype=torch.int32, device="cuda")
+    # the per-tile scale-4 byte kernel (forced) and the default scale-2 kernel
+    # both load their tile's pattern by a bulk copy; the scale-4 one is tested
+    monkeypatch.setenv("MERTENS_SIEVE_TILES", "1")
     monkeypatch.setenv("MERTENS_TEST_STALL_COPY", "1")
     with pytest.raises(pm.MertensError) as ei:
         pm.mertens_sieve_M(y1, length, 0, M)
