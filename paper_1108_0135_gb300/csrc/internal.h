@@ -134,12 +134,6 @@ inline void attrs_done(std::atomic<uint64_t> &done, uint64_t bit)
 int expand_M_enqueue(const int16_t *Mloc, const int64_t *segoff, uint64_t len, int32_t *M,
                      uint32_t *err, cudaStream_t s);
 
-// Device-wide exclusive scan of n uint32 values into out[0..n] (out[n] =
-// total).  `scratch` holds at least scan_scratch_words(n) uint32.
-size_t scan_scratch_words(size_t n);
-int exclusive_scan_u32(const uint32_t *in, uint32_t *out, size_t n, uint32_t *scratch,
-                       cudaStream_t s);
-
 // Thread-local last-error text.
 void set_last_error(const char *fmt, ...);
 

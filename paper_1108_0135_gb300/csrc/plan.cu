@@ -191,8 +191,11 @@ struct mertens_plan_s {
     // device buffers
     PrimeTable pt;
     uint64_t *dK = nullptr, *dJLO = nullptr, *dJC0 = nullptr, *dJCUR = nullptr, *dYCE = nullptr;
-    uint64_t *dJTOP = nullptr, *dJBOT = nullptr, *dS = nullptr, *dR = nullptr;
-    uint32_t *dICNT = nullptr, *dIOFF = nullptr, *dScan = nullptr;
+    uint64_t *dS = nullptr, *dR = nullptr;
+    // chunks of the global gather's heavy entries, per block (qcap records)
+    uint4 *dqueue = nullptr;
+    uint32_t *dqlen = nullptr;
+    uint32_t qcap = 0;
     int8_t *dmu_aux = nullptr;
     int16_t *dMloc[2] = {nullptr, nullptr};      // sieve output, two blocks in flight
     int32_t *dsegsum[2] = {nullptr, nullptr};
@@ -921,13 +924,28 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
     p->dJC0 = p->alloc<uint64_t>(E);
     p->dJCUR = p->alloc<uint64_t>(E);
     p->dYCE = p->alloc<uint64_t>(E);
-    p->dJTOP = p->alloc<uint64_t>(E);
-    p->dJBOT = p->alloc<uint64_t>(E);
     p->dS = p->alloc<uint64_t>(E);
     p->dR = p->alloc<uint64_t>(E);
-    p->dICNT = p->alloc<uint32_t>(E);
-    p->dIOFF = p->alloc<uint32_t>(E + 1);
-    p->dScan = p->alloc<uint32_t>(scan_scratch_words(E));
+    {
+        // chunk records of a block's global gather: an entry with cnt terms
+        // there posts ceil(cnt / kSparseItem) of them when cnt > 48; cnt is
+        // at most k (1/y_lo - 1/(y2+1)) + 1, so a block posts at most
+        // C/kSparseItem + min(E, C/48) with C = (sum k)(1/y_lo - 1/(y2+1)) + E
+        double most = 0;
+        for (uint64_t b = 0; b < p->nblocks; ++b) {
+            uint64_t y1, y2;
+            block_range(p, b, &y1, &y2);
+            const uint64_t ylo = std::max(p->gend[b] + 1, y1);
+            if (ylo > y2)
+                continue;
+            const double C = kpre[K.size()] * (1.0 / (double)ylo - 1.0 / ((double)y2 + 1.0)) +
+                             (double)E;
+            most = std::max(most, C / kSparseItem + std::min((double)E, C / 48.0));
+        }
+        p->qcap = (uint32_t)std::min(most * 1.01 + 256.0, 4.0e9);
+        p->dqueue = p->alloc<uint4>(p->qcap);
+        p->dqlen = p->alloc<uint32_t>(1);
+    }
     const uint64_t L = block_len;
     const uint64_t nseg = sieve_segments(L);
     // One stream by default: on GB300 the three-stream schedule measured
@@ -981,8 +999,8 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
     for (auto &a : p->allocs)
         if (!a.first)
             rc = MERTENS_ENOMEM;
-    bool any_null = !p->dK || !p->dJLO || !p->dJC0 || !p->dJCUR || !p->dYCE || !p->dJTOP ||
-                    !p->dJBOT || !p->dS || !p->dR || !p->dICNT || !p->dIOFF || !p->dScan ||
+    bool any_null = !p->dK || !p->dJLO || !p->dJC0 || !p->dJCUR || !p->dYCE || !p->dqueue ||
+                    !p->dqlen || !p->dS || !p->dR ||
                     (!table && (!p->dmu_aux || !p->dMloc[0] || !p->dsegsum[0] ||
                                 !p->dsegoff[0] || !p->dMloc[1] || !p->dsegsum[1] ||
                                 !p->dsegoff[1])) ||
@@ -1311,12 +1329,11 @@ static int run_enqueue(mertens_plan_s *p, cudaStream_t origin, uint64_t *out)
             sa.JC0 = p->dJC0;
             sa.YCE = p->dYCE;
             sa.MG = p->dMG;
-            sa.JCUR = p->dJCUR;
-            sa.JTOP = p->dJTOP;
-            sa.JBOT = p->dJBOT;
             sa.S = p->dS;
-            sa.ICNT = p->dICNT;
-            sa.IOFF = p->dIOFF;
+            sa.queue = p->dqueue;
+            sa.qlen = p->dqlen;
+            sa.qcap = p->qcap;
+            sa.err = p->derr;
             sa.Mloc = Mb;
             sa.segoff = Sb;
             sa.y_lo = p->gend[b] + 1 > y1 ? p->gend[b] + 1 : y1;
@@ -1348,7 +1365,7 @@ static int run_enqueue(mertens_plan_s *p, cudaStream_t origin, uint64_t *out)
                 launches += r;
             }
             ev_begin(p, kPhGather, s, &pe);
-            r = sparse_block_enqueue(sb, sa, p->dScan, s);
+            r = sparse_block_enqueue(sb, sa, s);
             ev_end(p, s, &pe);
             if (r < 0)
                 goto fail;
@@ -1510,6 +1527,10 @@ int mertens_result(mertens_plan_t p, size_t i, int64_t *M_n, int64_t *entries, s
     }
     if (err & kErrMOverflow) {
         set_last_error("mertens_result: |M(y)| exceeded the int32 block type");
+        return MERTENS_EOVERFLOW;
+    }
+    if (err & kErrQueue) {
+        set_last_error("mertens_result: the global gather's chunk queue overflowed");
         return MERTENS_EOVERFLOW;
     }
     if (len)
@@ -1731,6 +1752,18 @@ int mertens_window_result(mertens_plan_t p, size_t i, uint64_t *S_loc, uint64_t 
             set_last_error("mertens_window_result: %s", sieve_status_text(st));
             return sieve_status_code(st);
         }
+    }
+    uint32_t err = 0;
+    if (cudaMemcpy(&err, p->derr, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return MERTENS_ECUDA;
+    if (err & kErrTimeout) {
+        set_last_error("mertens_window_result: a bounded wait for a bulk copy in the update "
+                       "gave up");
+        return MERTENS_ETIMEOUT;
+    }
+    if (err & kErrQueue) {
+        set_last_error("mertens_window_result: the global gather's chunk queue overflowed");
+        return MERTENS_EOVERFLOW;
     }
     if (len)
         *len = p->X[i];

@@ -1920,89 +1920,4 @@ int expand_M_enqueue(const int16_t *Mloc, const int64_t *segoff, uint64_t len, i
     return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
-// ---------------------------------------------------------------------------
-// Device-wide exclusive scan of uint32 (three passes, no inter-CTA waits).
-// ---------------------------------------------------------------------------
-constexpr int kScanPer = 2048;  // values per CTA (256 threads x 8)
-
-__global__ void __launch_bounds__(256) scan_reduce_kernel(const uint32_t *__restrict__ in, size_t n,
-                                                          uint32_t *__restrict__ part)
-{
-    __shared__ uint32_t sh[33];
-    const size_t b = (size_t)blockIdx.x * kScanPer;
-    uint32_t s = 0;
-    for (int k = 0; k < 8; ++k) {
-        size_t i = b + (size_t)k * 256 + threadIdx.x;
-        if (i < n)
-            s += in[i];
-    }
-    uint32_t tot;
-    block_excl_scan<uint32_t>(s, sh, &tot);
-    if (threadIdx.x == 0)
-        part[blockIdx.x] = tot;
-}
-
-__global__ void __launch_bounds__(1024) scan_parts_kernel(uint32_t *__restrict__ part, uint32_t nparts,
-                                                          uint32_t *__restrict__ total_out)
-{
-    __shared__ uint32_t sh[33];
-    const uint32_t per = (nparts + blockDim.x - 1) / blockDim.x;
-    const uint32_t b = threadIdx.x * per, e = min(nparts, b + per);
-    uint32_t s = 0;
-    for (uint32_t i = b; i < e; ++i)
-        s += part[i];
-    uint32_t tot;
-    uint32_t run = block_excl_scan<uint32_t>(s, sh, &tot);
-    for (uint32_t i = b; i < e; ++i) {
-        uint32_t v = part[i];
-        part[i] = run;
-        run += v;
-    }
-    if (threadIdx.x == 0)
-        *total_out = tot;
-}
-
-__global__ void __launch_bounds__(256) scan_down_kernel(const uint32_t *__restrict__ in, size_t n,
-                                                        const uint32_t *__restrict__ part,
-                                                        uint32_t *__restrict__ out)
-{
-    __shared__ uint32_t sh[33];
-    const size_t b = (size_t)blockIdx.x * kScanPer + (size_t)threadIdx.x * 8;
-    uint32_t v[8], s = 0;
-    for (int k = 0; k < 8; ++k) {
-        size_t i = b + k;
-        v[k] = i < n ? in[i] : 0u;
-        s += v[k];
-    }
-    uint32_t tot;
-    uint32_t run = block_excl_scan<uint32_t>(s, sh, &tot) + part[blockIdx.x];
-    for (int k = 0; k < 8; ++k) {
-        size_t i = b + k;
-        if (i < n)
-            out[i] = run;
-        run += v[k];
-    }
-}
-
-size_t scan_scratch_words(size_t n)
-{
-    return (n + kScanPer - 1) / kScanPer + 1;
-}
-
-int exclusive_scan_u32(const uint32_t *in, uint32_t *out, size_t n, uint32_t *scratch,
-                       cudaStream_t s)
-{
-    const uint32_t nparts = (uint32_t)((n + kScanPer - 1) / kScanPer);
-    if (nparts == 0) {
-        cudaMemsetAsync(out, 0, 4, s);
-        return 1;
-    }
-    scan_reduce_kernel<<<nparts, 256, 0, s>>>(in, n, scratch);
-    scan_parts_kernel<<<1, 1024, 0, s>>>(scratch, nparts, out + n);
-    scan_down_kernel<<<nparts, 256, 0, s>>>(in, n, scratch, out);
-    if (cudaGetLastError() != cudaSuccess)
-        return -1;
-    return 3;
-}
-
 }  // namespace mert

@@ -217,75 +217,118 @@ __device__ __forceinline__ int64_t block_M(const int64_t *segoff, const int16_t 
     return segoff[i >> kSegShift] + (int64_t)Mloc[i];
 }
 
-// Per entry: the j-range of the global-memory part [y_lo, y2] of the block,
-// j in [max(jlo, floor(k/(y2+1))+1), min(jcur, floor(k/y_lo))] (so
-// floor(k/j) lies in it), its number of warp items, and the cursor for the
-// next block.  Also adds the boundary term -M(yc) floor(k/(yc+1)) of the
-// dense form when yc is in this block.
-__global__ void sparse_prep_kernel(SparseBlockArgs b, SparseArgs a)
+// M(floor(k/j)) of the block for four j at once: the four magic loads, then
+// the four M loads, so eight loads per lane are in flight instead of a chain.
+__device__ __forceinline__ int64_t block_M4(const SparseArgs &a, uint64_t k2, uint64_t y1,
+                                            const uint32_t j[4], const bool ok[4])
+{
+    uint64_t m[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+        m[u] = ok[u] ? a.MG[j[u]] : 0ull;
+    uint64_t i[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+        i[u] = ok[u] ? div_magic(k2, m[u], 32u - __clz(j[u] - 1u)) - y1 : 0ull;
+    int64_t s = 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+        if (ok[u])
+            s += block_M(a.segoff, a.Mloc, i[u]);
+    return s;
+}
+
+// Global-memory part [y_lo, y2] of block [y1, y2], one lane per entry: the
+// entry's j-range, j in [max(jlo, floor(k/(y2+1))+1), min(jc0, floor(k/y_lo))]
+// (so floor(k/j) lies in it; every earlier block's range ends above it).
+// Entries with at most kLaneTerms terms are summed here, four terms at a time;
+// heavier ones are posted as chunks of kSparseItem consecutive j (a
+// warp-aggregated slot count) for sparse_chunk_kernel.  Also adds the
+// boundary term -M(yc) floor(k/(yc+1)) of the dense form when yc is in the
+// block.
+__global__ void __launch_bounds__(256) sparse_range_kernel(SparseBlockArgs b, SparseArgs a)
 {
     const uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= a.nent)
-        return;
-    const uint64_t k2 = a.K[e] << 1;
-    const uint64_t jc = a.JCUR[e], jlo = a.JLO[e];
-    const uint64_t q1 = div_magic(k2, a.m_ylo, a.l_ylo);    // floor(k / y_lo)
-    const uint64_t q2 = div_magic(k2, b.m_y2p1, b.l_y2p1);  // floor(k / (y2+1))
-    const uint64_t jtop = jc < q1 ? jc : q1;
-    const uint64_t jbot = (q2 + 1) > jlo ? (q2 + 1) : jlo;
-    const uint64_t cnt = jtop >= jbot ? jtop - jbot + 1 : 0;
-    a.JTOP[e] = jtop;
-    a.JBOT[e] = jbot;
-    a.JCUR[e] = jc < q2 ? jc : q2;
-    uint64_t add = 0;
-    if (cnt <= kLaneTerms) {
-        // few terms: done here, by this thread
-        int64_t acc = 0;
-        for (uint64_t j = jbot; j <= jtop && cnt; ++j) {
-            const uint64_t y = div_magic(k2, a.MG[j], magic_shift(j));
-            acc += block_M(a.segoff, a.Mloc, y - b.y1);
-        }
-        add = (uint64_t)acc;
-        a.ICNT[e] = 0;
-    } else {
-        a.ICNT[e] = (uint32_t)((cnt + kSparseItem - 1) / kSparseItem);
+    const uint32_t lane = threadIdx.x & 31u;
+    const bool act = e < a.nent;
+    const uint64_t k2 = act ? a.K[e] << 1 : 0ull;
+    uint64_t jtop = 0, jbot = 1;
+    if (k2) {
+        const uint64_t q1 = div_magic(k2, a.m_ylo, a.l_ylo);    // floor(k / y_lo)
+        const uint64_t q2 = div_magic(k2, b.m_y2p1, b.l_y2p1);  // floor(k / (y2+1))
+        const uint64_t jc = a.JC0[e], jlo = a.JLO[e];
+        jtop = jc < q1 ? jc : q1;
+        jbot = (q2 + 1) > jlo ? (q2 + 1) : jlo;
     }
-    const uint64_t yc = a.YCE[e];
-    if (yc >= b.y1 && yc <= b.y2) {
-        const int64_t Myc = block_M(a.segoff, a.Mloc, yc - b.y1);
-        add -= (uint64_t)Myc * a.JC0[e];
+    const uint64_t cnt = jtop >= jbot ? jtop - jbot + 1 : 0;
+    int64_t add = 0;
+    if (cnt && cnt <= kLaneTerms) {
+        // j < 2^32 here (j <= sqrt(k))
+        for (uint32_t j0 = (uint32_t)jbot; j0 <= (uint32_t)jtop; j0 += 4u) {
+            const uint32_t j[4] = {j0, j0 + 1u, j0 + 2u, j0 + 3u};
+            const bool ok[4] = {true, j0 + 1u <= (uint32_t)jtop, j0 + 2u <= (uint32_t)jtop,
+                                j0 + 3u <= (uint32_t)jtop};
+            add += block_M4(a, k2, b.y1, j, ok);
+        }
+    }
+    if (k2) {
+        const uint64_t yc = a.YCE[e];
+        if (yc >= b.y1 && yc <= b.y2) {
+            const int64_t Myc = block_M(a.segoff, a.Mloc, yc - b.y1);
+            add -= (int64_t)((uint64_t)Myc * a.JC0[e]);
+        }
     }
     if (add)
         atomicAdd(reinterpret_cast<unsigned long long *>(a.S + e), (unsigned long long)add);
+    // heavy entries: ceil(cnt / kSparseItem) chunk records, slots taken with
+    // one atomic per warp
+    const uint32_t nch = cnt > kLaneTerms ? (uint32_t)((cnt + kSparseItem - 1) / kSparseItem) : 0u;
+    uint32_t incl = nch;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t nb = __shfl_up_sync(0xffffffffu, incl, o);
+        if ((int)lane >= o)
+            incl += nb;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total == 0)
+        return;
+    uint32_t base = 0;
+    if (lane == 31)
+        base = atomicAdd(a.qlen, total);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    uint32_t slot = base + incl - nch;
+    for (uint32_t c = 0; c < nch; ++c, ++slot) {
+        const uint64_t jt = jtop - (uint64_t)c * kSparseItem;
+        const uint64_t n = jt - jbot + 1 < (uint64_t)kSparseItem ? jt - jbot + 1 : kSparseItem;
+        if (slot < a.qcap)
+            a.queue[slot] = make_uint4((uint32_t)e, (uint32_t)jt, (uint32_t)(jt >> 32),
+                                       (uint32_t)n);
+        else
+            atomicOr(a.err, kErrQueue);
+    }
 }
 
-// One warp per item of kSparseItem consecutive j of one entry, lanes over j:
-// S[x] += sum M(floor(k/j)), M read from the block's M(y) array.
-__global__ void __launch_bounds__(256) sparse_update_kernel(SparseBlockArgs b, SparseArgs a)
+// The posted chunks, one warp per chunk (grid-stride): lanes over its j,
+// four terms per lane per round (sixteen loads in flight per lane).
+__global__ void __launch_bounds__(256) sparse_chunk_kernel(SparseBlockArgs b, SparseArgs a)
 {
-    const int lane = threadIdx.x & 31;
-    const uint32_t total = a.IOFF[a.nent];
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t q = *a.qlen;
+    const uint32_t total = q < a.qcap ? q : a.qcap;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total; w += nw) {
-        uint64_t lo = 0, hi = a.nent;  // largest e with IOFF[e] <= w
-        while (hi - lo > 1) {
-            const uint64_t mid = (lo + hi) >> 1;
-            if (a.IOFF[mid] <= w)
-                lo = mid;
-            else
-                hi = mid;
-        }
-        const uint64_t e = lo;
-        const uint64_t r = w - a.IOFF[e];
-        const uint64_t jt = a.JTOP[e] - r * kSparseItem;
-        const uint64_t jb0 = a.JBOT[e];
-        const uint64_t jb = (jt - jb0 + 1 > (uint64_t)kSparseItem) ? jt - kSparseItem + 1 : jb0;
+        const uint4 r = a.queue[w];
+        const uint64_t e = r.x;
+        const uint64_t jt = (uint64_t)r.y | ((uint64_t)r.z << 32);
+        const uint32_t n = r.w;  // terms j = jt - n + 1 .. jt; jt <= sqrt(k) < 2^32
         const uint64_t k2 = a.K[e] << 1;
         int64_t acc = 0;
-        const uint64_t *mp = a.MG + (jt - lane);
-        for (uint64_t j = jt - lane; j >= jb && j <= jt; j -= 32, mp -= 32) {
-            const uint64_t y = div_magic(k2, *mp, magic_shift(j));
-            acc += block_M(a.segoff, a.Mloc, y - b.y1);
+        for (uint32_t i = lane; i < n; i += 128u) {
+            const uint32_t j[4] = {(uint32_t)jt - i, (uint32_t)jt - i - 32u, (uint32_t)jt - i - 64u,
+                                   (uint32_t)jt - i - 96u};
+            const bool ok[4] = {true, i + 32u < n, i + 64u < n, i + 96u < n};
+            acc += block_M4(a, k2, b.y1, j, ok);
         }
         acc = warp_sum_i64(acc);
         if (lane == 0)
@@ -696,23 +739,16 @@ int dense_update_enqueue(const DenseArgs &a, cudaStream_t s)
     return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
-int sparse_block_enqueue(const SparseBlockArgs &b, const SparseArgs &a, uint32_t *scan_scratch,
-                         cudaStream_t s)
+int sparse_block_enqueue(const SparseBlockArgs &b, const SparseArgs &a, cudaStream_t s)
 {
-    int launches = 0;
     const unsigned pb = (unsigned)((a.nent + 255) / 256);
-    sparse_prep_kernel<<<pb, 256, 0, s>>>(b, a);
-    ++launches;
-    int r = exclusive_scan_u32(a.ICNT, a.IOFF, a.nent, scan_scratch, s);
-    if (r < 0)
-        return -1;
-    launches += r;
+    cudaMemsetAsync(a.qlen, 0, 4, s);
+    sparse_range_kernel<<<pb, 256, 0, s>>>(b, a);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    sparse_update_kernel<<<sms * 8, 256, 0, s>>>(b, a);
-    ++launches;
-    return cudaGetLastError() == cudaSuccess ? launches : -1;
+    sparse_chunk_kernel<<<sms * 8, 256, 0, s>>>(b, a);
+    return cudaGetLastError() == cudaSuccess ? 2 : -1;
 }
 
 // ---------------------------------------------------------------------------

@@ -51,17 +51,25 @@ struct SparseBlockArgs {
 };
 
 // M(y) of the current block: segoff[(y - y1) >> kSegShift] + Mloc[y - y1].
+// Chunks of heavy entries go to `queue` ({entry, j_top low, j_top high,
+// terms}, qlen of them, at most qcap; beyond that kErrQueue in *err).
 struct SparseArgs {
     uint64_t nent;
     uint64_t y_lo;  // first y of the block handled by the global-memory path
     uint64_t m_ylo;
     uint32_t l_ylo;
+    uint32_t qcap;
     const uint64_t *K, *JLO, *JC0, *YCE, *MG;
-    uint64_t *JCUR, *JTOP, *JBOT, *S;
-    uint32_t *ICNT, *IOFF;
+    uint64_t *S;
+    uint4 *queue;
+    uint32_t *qlen;
+    uint32_t *err;
     const int16_t *Mloc;
     const int64_t *segoff;
 };
+
+// Status bit of a plan: the global gather's chunk queue overflowed.
+constexpr uint32_t kErrQueue = 16u;
 
 struct QueryDev {
     uint64_t X;    // entries of the target
@@ -149,8 +157,7 @@ int wide_update_enqueue(const WideArgs &a, uint32_t nw, uint32_t grid_x, cudaStr
 int dense_list_enqueue(const int8_t *mu_aux, uint64_t ydense, const uint64_t *MG, uint64_t *dl_m,
                        uint16_t *dl_yo, uint32_t *dl_cnt, cudaStream_t s);
 int dense_update_enqueue(const DenseArgs &a, cudaStream_t s);
-int sparse_block_enqueue(const SparseBlockArgs &b, const SparseArgs &a, uint32_t *scan_scratch,
-                         cudaStream_t s);
+int sparse_block_enqueue(const SparseBlockArgs &b, const SparseArgs &a, cudaStream_t s);
 int gather_tiles_enqueue(const GatherArgs &a, cudaStream_t s);
 // Exchange buffers (two int64 words per entry: the low and the high 32-bit
 // half of its 64-bit sum): add S_loc + C coef of a window; turn one back into
