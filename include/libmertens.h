@@ -103,12 +103,14 @@ int mertens_plan(mertens_plan_t *out, const mertens_u128 *n, size_t count,
  * 1 <= y <= y_max) is computed once and kept in device memory (about
  * 2 bytes per y), together with what the update needs independently of the
  * target for all n <= n_max (the divisor magics and the squarefree list of
- * the dense form).  Plans made on it run only the update and resolve, with
- * the sieve limit u as large as the table allows (u = min(n, y_max + 1); the
- * update's terms fall as 1/sqrt(u)); a target n <= y_max is read from the
- * table directly.  The paper sieves per target (Sec. 3); sharing one sieve
- * between queries is what Sec. 2 allows for close targets, taken to every
- * target the table covers.
+ * the dense form).  Plans made on it read M(y) from the table for every sieve
+ * block that ends at or below y_max and sieve only the blocks above it; their
+ * sieve limit u is at least min(n, y_max + 1) (the table's part of the sieve
+ * costs nothing and the update's terms fall as 1/sqrt(u)) and at least the
+ * automatic limit of a sieving plan for the same targets; a target
+ * n <= y_max is read from the table directly.  The paper sieves per target
+ * (Sec. 3); sharing one sieve between queries is what Sec. 2 allows for close
+ * targets, taken to every target the table covers.
  *
  *   mertens_table_create: 1 <= y_max < 2^40, 1 <= n_max < 2^127; sieves on
  *     `stream` and returns when done.  The table lives on the current device
@@ -117,9 +119,9 @@ int mertens_plan(mertens_plan_t *out, const mertens_u128 *n, size_t count,
  *   mertens_table_info: y_max, n_max and the device bytes held (each output
  *     may be NULL).  Errors: MERTENS_EINVAL (NULL table).
  *   mertens_plan_on_table: as mertens_plan, on the table's device; u = {0,0}
- *     picks min(n, y_max + 1) per target.  MERTENS_ENOTSUP when a target
- *     exceeds n_max or needs y, dense cut-offs or divisors beyond the table
- *     (for example when y_max + 1 <= sqrt(n)); block_len must be a multiple of
+ *     picks the larger of min(n, y_max + 1) and the automatic limit per
+ *     target.  MERTENS_ENOTSUP when a target exceeds n_max or needs dense
+ *     cut-offs or divisors beyond the table; block_len must be a multiple of
  *     2048 (0: 2^30).  The table must outlive its plans.
  *   mertens_table_destroy: waits for the device, then frees the table.
  */

@@ -183,6 +183,7 @@ struct mertens_plan_s {
     // are the table's; targets n <= table y_max are read from it directly
     // (entry, y) pairs
     mertens_table_s *table = nullptr;
+    bool sieves = true;  // some block is sieved (always without a table)
     std::vector<uint64_t> lookups;
     uint64_t *dlook = nullptr;
     mertens_tuning tuning{};
@@ -365,12 +366,16 @@ size_t plan_device_bytes(mertens_plan_t p)
 }
 }  // namespace mert
 
-// Sieve limit of a target on a resident table of M(y), y <= y_max: as large
-// as the table allows (the update's terms fall as 1/sqrt(u)).
-static uint64_t table_u(u128 n, uint64_t y_max)
+// Sieve limit of a target on a resident table of M(y), y <= y_max: at least
+// as large as the table reaches (its part of the sieve costs nothing, and the
+// update's terms fall as 1/sqrt(u)), and at least the automatic limit of a
+// sieving plan; blocks above y_max are sieved as usual.
+static uint64_t on_table_u(u128 n, double ub, uint64_t y_max)
 {
-    const u128 u = (u128)y_max + 1;
-    return (uint64_t)(n < u ? n : u);
+    const u128 t = (u128)y_max + 1;
+    const uint64_t ut = (uint64_t)(n < t ? n : t);
+    const uint64_t ua = target_u(n, ub);
+    return ut > ua ? ut : ua;
 }
 
 static int check_u(u128 n, uint64_t u)
@@ -501,15 +506,13 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
         }
         if (table) {
             const u128 nmax = ((u128)table->n_max_hi << 64) | table->n_max_lo;
-            const uint64_t ut = u.lo ? u.lo : table_u(nn, table->y_max);
-            if (nn > nmax || (nn > table->y_max && (ut > table->y_max + 1 ||
-                                                     check_u(nn, ut) != MERTENS_OK))) {
-                set_last_error("mertens_plan_on_table: n[%zu] is beyond the table (n_max, or "
-                               "u <= y_max + 1 with u > sqrt(n))", i);
+            if (nn > nmax) {
+                set_last_error("mertens_plan_on_table: n[%zu] is beyond the table's n_max", i);
                 return MERTENS_ENOTSUP;
             }
         }
-        const uint64_t uu = u.lo ? u.lo : (table ? table_u(nn, table->y_max) : target_u(nn, ub));
+        const uint64_t uu = u.lo ? u.lo : (table ? on_table_u(nn, ub, table->y_max)
+                                                 : target_u(nn, ub));
         if (nn / uu >= ((u128)1 << 32)) {
             set_last_error("mertens_plan: n[%zu]/u >= 2^32 array entries", i);
             return MERTENS_ENOTSUP;
@@ -528,7 +531,8 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
     std::vector<Group> groups;
     for (size_t i = 0; i < count; ++i) {
         const u128 nn = to_u128(n[i]);
-        const uint64_t uu = u.lo ? u.lo : (table ? table_u(nn, table->y_max) : target_u(nn, ub));
+        const uint64_t uu = u.lo ? u.lo : (table ? on_table_u(nn, ub, table->y_max)
+                                                 : target_u(nn, ub));
         const uint64_t X = (uint64_t)(nn / uu);
         p->n.push_back((uint64_t)nn);
         p->n_hi.push_back((uint64_t)(nn >> 64));
@@ -723,9 +727,8 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
         else if (e[0] == '2')
             p->gquot = 2;
     }
-    if (table && (p->y_max > table->y_max || p->ydense > table->ydense ||
-                  p->mg_n > table->mg_n)) {
-        set_last_error("mertens_plan_on_table: the targets need y, dense cut-offs or divisors "
+    if (table && (p->ydense > table->ydense || p->mg_n > table->mg_n)) {
+        set_last_error("mertens_plan_on_table: the targets need dense cut-offs or divisors "
                        "beyond the table");
         delete p;
         return MERTENS_ENOTSUP;
@@ -952,6 +955,8 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
     // slower (the sieve and the updates contend for the same SM resources);
     // MERTENS_OVERLAP=1 selects it.  Plans on a table have no sieve.
     p->serial = getenv("MERTENS_OVERLAP") == nullptr || p->nblocks == 1 || table;
+    // a plan on a table sieves only the blocks that end above the table
+    p->sieves = !table || p->y_last > table->y_max;
     if (table) {
         // the table's M(y) blocks are addressed per block at run time
         p->dmu_aux = nullptr;
@@ -962,8 +967,10 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
         p->mg_built = true;
         if (!p->lookups.empty())
             p->dlook = p->alloc<uint64_t>(p->lookups.size());
-    } else {
-        p->dmu_aux = p->alloc<int8_t>(p->ydense + 16);
+    }
+    if (p->sieves) {
+        if (!table)
+            p->dmu_aux = p->alloc<int8_t>(p->ydense + 16);
         const int nbuf = p->serial ? 1 : 2;
         for (int i = 0; i < 2; ++i) {
             if (i < nbuf) {
@@ -976,10 +983,12 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
                 p->dsegoff[i] = p->dsegoff[0];
             }
         }
-        p->dMG = p->alloc<uint64_t>(p->mg_n + 1);
-        p->ddl_m = p->alloc<uint64_t>(nchunks * kChunkCapPad);
-        p->ddl_yo = p->alloc<uint16_t>(nchunks * kChunkCapPad);
-        p->ddl_cnt = p->alloc<uint32_t>(nchunks);
+        if (!table) {
+            p->dMG = p->alloc<uint64_t>(p->mg_n + 1);
+            p->ddl_m = p->alloc<uint64_t>(nchunks * kChunkCapPad);
+            p->ddl_yo = p->alloc<uint16_t>(nchunks * kChunkCapPad);
+            p->ddl_cnt = p->alloc<uint32_t>(nchunks);
+        }
     }
     p->dcarry = p->alloc<int64_t>(p->nblocks + 1);
     p->dgtiles = p->alloc<GatherTile>(gtiles.size() + 1);
@@ -1001,9 +1010,9 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
             rc = MERTENS_ENOMEM;
     bool any_null = !p->dK || !p->dJLO || !p->dJC0 || !p->dJCUR || !p->dYCE || !p->dqueue ||
                     !p->dqlen || !p->dS || !p->dR ||
-                    (!table && (!p->dmu_aux || !p->dMloc[0] || !p->dsegsum[0] ||
-                                !p->dsegoff[0] || !p->dMloc[1] || !p->dsegsum[1] ||
-                                !p->dsegoff[1])) ||
+                    (!table && !p->dmu_aux) ||
+                    (p->sieves && (!p->dMloc[0] || !p->dsegsum[0] || !p->dsegoff[0] ||
+                                   !p->dMloc[1] || !p->dsegsum[1] || !p->dsegoff[1])) ||
                     (!p->lookups.empty() && !p->dlook) || !p->dgtiles ||
                     !p->dcounter_dense || !p->dcounter_gather ||
                     !p->dgitems || !p->dcarry || !p->derr || !p->dcounter || !p->dMG ||
@@ -1011,14 +1020,14 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
                     !p->dqs || (!p->wide.empty() && !p->dwide) || (window && !p->dcoef);
     if (any_null)
         rc = MERTENS_ENOMEM;
-    if (rc == MERTENS_OK && !table) {
+    if (rc == MERTENS_OK && p->sieves) {
         int prc = prime_table_create(&p->pt, p->al, std::max<uint64_t>(p->y_last, 1), nullptr);
         if (prc == 0)
             prc = sieve_scratch_create(&p->pt, block_len);
         if (prc != 0)
             rc = prc == 6 ? MERTENS_ENOTSUP : (prc == 2 ? MERTENS_ENOMEM : MERTENS_ECUDA);
     }
-    if (rc == MERTENS_OK && !table) {
+    if (rc == MERTENS_OK && p->sieves) {
         // algorithmic sieve updates: each block of length len sieved with the
         // primes p <= max(7, sqrt(block end)) costs len * sum (1/p + 1/p^2)
         std::vector<double> pre(p->pt.np + 1, 0.0);
@@ -1029,6 +1038,8 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
         for (uint64_t b = 0; b < p->nblocks; ++b) {
             uint64_t y1, y2;
             block_range(p, b, &y1, &y2);
+            if (table && y2 <= table->y_max)
+                continue;  // read from the table
             const uint64_t P = std::max<uint64_t>(7, isqrt64(y2));
             p->sieve_updates += (double)(y2 - y1 + 1) * pre[prime_count_upto(&p->pt, P)];
         }
@@ -1243,13 +1254,24 @@ static int run_enqueue(mertens_plan_s *p, cudaStream_t origin, uint64_t *out)
             uint64_t y1, y2;
             block_range(p, b, &y1, &y2);
             const int buf = (int)(b & 1);
-            // M(y) of the block: the plan's buffer (sieved below) or the table's
-            const int16_t *Mb = tab ? tab->Mloc + (y1 - 1) : p->dMloc[buf];
-            const int64_t *Sb = tab ? tab->segoff + ((y1 - 1) >> kSegShift) : p->dsegoff[buf];
+            // M(y) of the block: the table's where it covers the whole block,
+            // else the plan's buffer (sieved below)
+            const bool from_table = tab && y2 <= tab->y_max;
+            const int16_t *Mb = from_table ? tab->Mloc + (y1 - 1) : p->dMloc[buf];
+            const int64_t *Sb =
+                from_table ? tab->segoff + ((y1 - 1) >> kSegShift) : p->dsegoff[buf];
             if (!serial && b >= 2)
                 cudaStreamWaitEvent(ss, p->ev_upd[b - 2], 0);
             cudaStream_t s = ss;
-            if (!tab) {
+            if (tab && !from_table && y1 > 1 && y1 - 1 <= tab->y_max) {
+                // the first sieved block above the table: its carry M(y1 - 1)
+                // is the table's
+                r = carry_from_table_enqueue(tab->Mloc, tab->segoff, y1 - 1, p->dcarry + b, ss);
+                if (r < 0)
+                    goto fail;
+                launches += r;
+            }
+            if (!from_table) {
                 SieveLaunch L;
                 L.y1 = y1;
                 L.len = y2 - y1 + 1;
@@ -1514,7 +1536,7 @@ int mertens_result(mertens_plan_t p, size_t i, int64_t *M_n, int64_t *entries, s
     uint32_t err = 0;
     if (cudaMemcpy(&err, p->derr, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
         return MERTENS_ECUDA;
-    if (!p->table) {
+    if (p->sieves) {
         const uint32_t st = sieve_scratch_status(&p->pt);
         if (st) {
             set_last_error("mertens_result: %s", sieve_status_text(st));
@@ -1630,7 +1652,7 @@ int mertens_window_accumulate(mertens_plan_t p, size_t i, const int64_t *mu_befo
         set_last_error("mertens_window_accumulate: mertens_run was not called");
         return MERTENS_ENOTREADY;
     }
-    if (!p->table) {
+    if (p->sieves) {
         // the sieve's status words are read after the run has finished
         if (cudaEventSynchronize(p->done) != cudaSuccess) {
             set_last_error("mertens_window_accumulate: %s", cudaGetErrorString(cudaGetLastError()));
@@ -1746,7 +1768,7 @@ int mertens_window_result(mertens_plan_t p, size_t i, uint64_t *S_loc, uint64_t 
         set_last_error("mertens_window_result: %s", cudaGetErrorString(cudaGetLastError()));
         return MERTENS_ECUDA;
     }
-    if (!p->table) {
+    if (p->sieves) {
         const uint32_t st = sieve_scratch_status(&p->pt);
         if (st) {
             set_last_error("mertens_window_result: %s", sieve_status_text(st));
@@ -1854,6 +1876,16 @@ int mertens_run_stats_get(mertens_plan_t p, mertens_run_stats *st)
         return MERTENS_ECUDA;
     st->blocks = p->nblocks;
     st->y_sieved = p->y_last >= p->y_first ? p->y_last - p->y_first + 1 : 0;
+    if (p->table) {
+        // blocks read from the table are not sieved
+        st->y_sieved = 0;
+        for (uint64_t b = 0; b < p->nblocks; ++b) {
+            uint64_t y1, y2;
+            block_range(p, b, &y1, &y2);
+            if (y2 > p->table->y_max)
+                st->y_sieved += y2 - y1 + 1;
+        }
+    }
     st->terms = p->terms;
     st->kernels = p->kernels;
     st->dense_y = p->dense_y;

@@ -57,13 +57,21 @@ struct Inflight {
     size_t bytes = 0;
 };
 
-// Device memory of a batch planned on a resident table: entry arrays only.
+// Device memory of a batch planned on a resident table: entry arrays, and a
+// sieving plan's buffers when the batch's sieve limit reaches above the table
+// (those blocks are sieved).
+size_t estimate_batch_bytes(const std::vector<uint64_t> &ns);
 size_t estimate_table_batch_bytes(const std::vector<uint64_t> &ns, uint64_t y_max)
 {
+    const std::vector<uint64_t> us = plan_auto_u(ns);
     double entries = 0;
-    for (uint64_t n : ns)
-        entries += (double)(n / std::min<uint64_t>(n, y_max + 1));
-    return (size_t)(110.0 * entries + 64.0e6);
+    bool above = false;
+    for (size_t i = 0; i < ns.size(); ++i) {
+        const uint64_t u = std::max<uint64_t>(us[i], std::min<uint64_t>(ns[i], y_max + 1));
+        entries += (double)(ns[i] / u);
+        above = above || u > y_max + 1;
+    }
+    return above ? estimate_batch_bytes(ns) : (size_t)(110.0 * entries + 64.0e6);
 }
 
 // Device memory a batch's plan will take, estimated from the plan's shapes

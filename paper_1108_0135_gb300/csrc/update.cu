@@ -814,6 +814,20 @@ __global__ void table_lookup_kernel(const uint64_t *__restrict__ pairs, uint32_t
     R[pairs[2 * i]] = (uint64_t)(segoff[(y - 1) >> kSegShift] + (int64_t)Mloc[y - 1]);
 }
 
+__global__ void carry_from_table_kernel(const int16_t *__restrict__ Mloc,
+                                        const int64_t *__restrict__ segoff, uint64_t y,
+                                        int64_t *__restrict__ out)
+{
+    *out = segoff[(y - 1) >> kSegShift] + (int64_t)Mloc[y - 1];
+}
+
+int carry_from_table_enqueue(const int16_t *Mloc, const int64_t *segoff, uint64_t y,
+                             int64_t *out, cudaStream_t s)
+{
+    carry_from_table_kernel<<<1, 1, 0, s>>>(Mloc, segoff, y, out);
+    return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
 int table_lookup_enqueue(const uint64_t *pairs, uint32_t count, const int16_t *Mloc,
                          const int64_t *segoff, uint64_t *R, cudaStream_t s)
 {

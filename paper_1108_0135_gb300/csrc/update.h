@@ -153,6 +153,9 @@ int magic_table_enqueue(uint64_t *MG, uint64_t nd, cudaStream_t s);
 // R[pairs[2i]] = M(pairs[2i+1]) from a resident table (i < count).
 int table_lookup_enqueue(const uint64_t *pairs, uint32_t count, const int16_t *Mloc,
                          const int64_t *segoff, uint64_t *R, cudaStream_t s);
+// *out = M(y) from a resident table (1 <= y <= its y_max).
+int carry_from_table_enqueue(const int16_t *Mloc, const int64_t *segoff, uint64_t y,
+                             int64_t *out, cudaStream_t s);
 int wide_update_enqueue(const WideArgs &a, uint32_t nw, uint32_t grid_x, cudaStream_t s);
 int dense_list_enqueue(const int8_t *mu_aux, uint64_t ydense, const uint64_t *MG, uint64_t *dl_m,
                        uint16_t *dl_yo, uint32_t *dl_cnt, cudaStream_t s);

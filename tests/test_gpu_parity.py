@@ -727,11 +727,21 @@ def test_table_lookups_are_the_sieve(table_2e26):
 
 @pytest.mark.parametrize("n,block_len", [
     (10**12, 0), (10**12 + 12345, 2**22), (7 * 10**12 + 1, 2**20 + 2048), (2**26 + 12346, 0),
-    (10**13, 0),
+    (10**13, 0), (10**13 - 77, 2**22),
 ])
 def test_plans_on_table_match_oracle(table_2e26, n, block_len):
-    (m, arr), = _run_on_table(table_2e26, [n], 0, block_len)
-    u = min(n, 2**26 + 12346)
+    """u is at least what the table reaches (min(n, y_max + 1)); where the
+    automatic u is larger (10^13: about 2.1e8 against 2^26 + 12346) the blocks
+    above the table are sieved and the carry into the first of them is the
+    table's M(y)."""
+    plan = pm.mertens_plan_on_table(table_2e26, [n], 0, block_len)
+    try:
+        u = pm.mertens_plan_info(plan, 0)["u"]
+        pm.mertens_run(plan)
+        m, arr = pm.mertens_result(plan, 0, entries=True)
+    finally:
+        pm.mertens_destroy(plan)
+    assert u >= min(n, 2**26 + 12346)
     assert len(arr) == n // u
     assert np.array_equal(arr, oracle.mertens_array(n, n // u, L=10**8))
     # and a sieving plan with the same u agrees
@@ -750,10 +760,18 @@ def test_two_word_entries_on_table(table_2e26, monkeypatch):
 
 
 def test_batch_on_table_same_as_alone(table_2e26):
+    """Each target of a batch on the table, alone on the table with the
+    batch's u for it, gives the same whole array."""
     ns = [10**12 + 7, 3 * 10**11, 5 * 10**7, 10**13, 123_456_789_012]
-    batch = _run_on_table(table_2e26, ns)
-    for n, (m, arr) in zip(ns, batch):
-        (m1, arr1), = _run_on_table(table_2e26, [n])
+    plan = pm.mertens_plan_on_table(table_2e26, ns)
+    try:
+        us = [pm.mertens_plan_info(plan, i)["u"] for i in range(len(ns))]
+        pm.mertens_run(plan)
+        batch = [pm.mertens_result(plan, i, entries=True) for i in range(len(ns))]
+    finally:
+        pm.mertens_destroy(plan)
+    for n, u, (m, arr) in zip(ns, us, batch):
+        (m1, arr1), = _run_on_table(table_2e26, [n], u)
         assert m == m1 and np.array_equal(arr, arr1), n
 
 
@@ -763,13 +781,15 @@ def test_table_refuses_what_it_cannot_serve(table_2e26):
     assert ei.value.code == pm.MERTENS_ENOTSUP
     small = pm.mertens_table_create(10**5, 10**12)
     try:
-        with pytest.raises(pm.MertensError) as ei:
-            pm.mertens_plan_on_table(small, [10**12])           # sqrt(n) > y_max
-        assert ei.value.code == pm.MERTENS_ENOTSUP
         with pytest.raises(pm.MertensError):
             pm.mertens_plan_on_table(small, [10**9], 0, 1000)   # block not a multiple of 2048
         (m, _), = _run_on_table(small, [10**9])
         assert m == oracle.mertens(10**9, L=10**6)
+        # the dense cut-offs of 10^12 (about 1.4e6) lie beyond the table's
+        # squarefree list (y <= 10^5)
+        with pytest.raises(pm.MertensError) as ei:
+            pm.mertens_plan_on_table(small, [10**12])
+        assert ei.value.code == pm.MERTENS_ENOTSUP
     finally:
         pm.mertens_table_destroy(small)
 
