@@ -215,6 +215,7 @@ struct mertens_plan_s {
     GatherItem *dgitems = nullptr;
     std::vector<uint32_t> gblk;
     std::vector<uint64_t> gend;
+    std::vector<uint64_t> ktile;  // per block: entries with k >= this take its tiles
     uint64_t gather_smem_end = 0;
     uint32_t *derr = nullptr, *dcounter = nullptr;
     uint64_t *dMG = nullptr, *ddl_m = nullptr;
@@ -804,12 +805,39 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
     std::vector<GatherTile> gtiles;
     std::vector<GatherItem> gitems;
     std::vector<std::pair<uint64_t, uint64_t>> ranges;
+    // Blocks above the tile range: tiles over the whole block for the
+    // entries with k >= kt_fac y1^2 / kGatherTile (about kt_fac terms or more
+    // per tile; a prefix of each target's entries), when they have at least
+    // kt_min terms per tile together; the global path takes the others.
+    double kt_fac = 1.0, kt_min = 700.0;
+    if (const char *e = getenv("MERTENS_TILE_KT"))
+        kt_fac = atof(e);
+    if (const char *e = getenv("MERTENS_TILE_MIN"))
+        kt_min = atof(e);
     for (uint64_t b = 0; b < p->nblocks; ++b) {
         uint64_t y1, y2;
         block_range(p, b, &y1, &y2);
         p->gblk.push_back((uint32_t)gitems.size());
-        const uint64_t end = std::min(y2, p->gather_smem_end);
+        uint64_t end = std::min(y2, p->gather_smem_end);
         p->gend.push_back(y1 <= end ? end : y1 - 1);
+        uint64_t kt = UINT64_MAX;  // entries with k >= kt take this block's tiles
+        if (y1 > p->gather_smem_end && kt_fac > 0) {
+            const double k0 = kt_fac * (double)y1 * (double)y1 / kGatherTile;
+            double ksum = 0;
+            for (size_t i = 0; i < count; ++i) {
+                const uint64_t o = p->off[i], X = p->X[i];
+                const double xt = std::min((double)X,
+                                           std::floor(((double)p->n[i] +
+                                                       18446744073709551616.0 *
+                                                           (double)p->n_hi[i]) / k0));
+                ksum += kpre[o + (uint64_t)xt] - kpre[o];
+            }
+            if (ksum * kGatherTile / ((double)y1 * (double)y1) >= kt_min) {
+                kt = (uint64_t)std::ceil(k0);
+                end = y2;
+            }
+        }
+        p->ktile.push_back(kt);
         for (uint64_t t1 = y1; t1 <= end; t1 += kGatherTile) {
             const uint64_t t2 = std::min(t1 + kGatherTile - 1, end);
             GatherTile T;
@@ -836,12 +864,26 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
                     else
                         lo = mid + 1;
                 }
-                if (lo >= X)
+                // above the tile range only the prefix with k >= kt
+                uint64_t top = X;
+                if (kt != UINT64_MAX) {
+                    uint64_t a = 0, z = X;  // first x index with k < kt
+                    while (a < z) {
+                        const uint64_t mid = (a + z) / 2;
+                        if (K[o + mid] >= kt || K[o + mid] == 0)
+                            a = mid + 1;
+                        else
+                            z = mid;
+                    }
+                    top = a;
+                }
+                if (lo >= top)
                     continue;
-                if (!ranges.empty() && o + lo <= ranges.back().second + 4096)
-                    ranges.back().second = o + X;
+                if (!ranges.empty() && o + lo <= ranges.back().second + 4096 &&
+                    kt == UINT64_MAX)
+                    ranges.back().second = o + top;
                 else
-                    ranges.push_back({o + lo, o + X});
+                    ranges.push_back({o + lo, o + top});
             }
             // work of entries [f, g): about one range check each plus
             // sum k * len / t1^2 gathered terms; items of ~kItemWork
@@ -1359,6 +1401,7 @@ static int run_enqueue(mertens_plan_s *p, cudaStream_t origin, uint64_t *out)
             sa.Mloc = Mb;
             sa.segoff = Sb;
             sa.y_lo = p->gend[b] + 1 > y1 ? p->gend[b] + 1 : y1;
+            sa.kmax = p->ktile[b];
             sa.m_ylo = magic_of(sa.y_lo);
             sa.l_ylo = magic_shift(sa.y_lo);
             if (p->gblk[b + 1] > p->gblk[b]) {

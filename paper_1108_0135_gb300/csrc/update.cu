@@ -238,7 +238,8 @@ __device__ __forceinline__ int64_t block_M4(const SparseArgs &a, uint64_t k2, ui
     return s;
 }
 
-// Global-memory part [y_lo, y2] of block [y1, y2], one lane per entry: the
+// Global-memory part [y_lo, y2] of block [y1, y2], one lane per entry (those
+// with k < kmax; the others take the block's shared-memory tiles): the
 // entry's j-range, j in [max(jlo, floor(k/(y2+1))+1), min(jc0, floor(k/y_lo))]
 // (so floor(k/j) lies in it; every earlier block's range ends above it).
 // Entries with at most kLaneTerms terms are summed here, four terms at a time;
@@ -251,9 +252,10 @@ __global__ void __launch_bounds__(256) sparse_range_kernel(SparseBlockArgs b, Sp
     const uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t lane = threadIdx.x & 31u;
     const bool act = e < a.nent;
-    const uint64_t k2 = act ? a.K[e] << 1 : 0ull;
+    const uint64_t k = act ? a.K[e] : 0ull;
+    const uint64_t k2 = k << 1;
     uint64_t jtop = 0, jbot = 1;
-    if (k2) {
+    if (k2 && k < a.kmax) {
         const uint64_t q1 = div_magic(k2, a.m_ylo, a.l_ylo);    // floor(k / y_lo)
         const uint64_t q2 = div_magic(k2, b.m_y2p1, b.l_y2p1);  // floor(k / (y2+1))
         const uint64_t jc = a.JC0[e], jlo = a.JLO[e];

@@ -56,6 +56,7 @@ struct SparseBlockArgs {
 struct SparseArgs {
     uint64_t nent;
     uint64_t y_lo;  // first y of the block handled by the global-memory path
+    uint64_t kmax;  // entries with k >= kmax have their terms in the block's tiles
     uint64_t m_ylo;
     uint32_t l_ylo;
     uint32_t qcap;
