@@ -674,12 +674,12 @@ def window_measure(stream):
 #     class's main kernel (share of cycles a scheduler issued an instruction);
 #   pipe: the busiest pipe of that kernel and its share of active cycles.
 NCU = {
-    "mu_sieve": {"kernel": "mu_sieve_byte_kernel", "dram_bytes_per_step": 150 * 477.351e6,
-                 "issue_active": 0.621, "pipe": ("alu", 0.463)},
-    "update_dense": {"kernel": "dense_update_kernel", "dram_bytes_per_step": 870.43e6,
-                     "issue_active": 0.485, "pipe": ("fmaheavy", 0.87)},
-    "update_gathered": {"kernel": "gather_tile_kernel", "dram_bytes_per_step": None,
-                        "issue_active": 0.886, "pipe": ("alu", 0.618)},
+    "mu_sieve": {"kernel": "mu_sieve_t2_kernel", "dram_bytes_per_step": 72.9e9,
+                 "issue_active": 0.605, "pipe": ("alu", 0.385)},
+    "update_dense": {"kernel": "dense_update_kernel", "dram_bytes_per_step": 0.872e9,
+                     "issue_active": 0.485, "pipe": ("fmaheavy", 0.874)},
+    "update_gathered": {"kernel": "gather_tile_kernel", "dram_bytes_per_step": 19.25e9,
+                        "issue_active": 0.886, "pipe": ("alu", 0.619)},
 }
 # Issue slots of the chip: 152 SMs x 4 schedulers x one warp instruction per
 # clock at the maximum SM clock.
