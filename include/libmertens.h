@@ -78,8 +78,9 @@ int mertens_set_allocator(mertens_alloc_fn alloc, mertens_free_fn release, void 
  *              all others with one-word quotients.  Copied; the caller
  *              keeps ownership.
  *   u          sieve limit shared by all targets.  {0,0} = chosen by the
- *              library: a batch limit ub = f (sum n)^(2/3) Neff^(-1/5),
- *              Neff = sum n / max n (f from mertens_tuning), and per target
+ *              library: a batch limit ub = f g (sum n)^(2/3) (f from
+ *              mertens_tuning, g = clamp((max n/1e18)^(-1/4), 1, 1.78)),
+ *              and per target
  *              u_i = min(n_i, ub), raised above floor(sqrt(n_i)) where
  *              needed; the sieve runs to the largest targets' need.  Otherwise it must
  *              satisfy floor(sqrt(n_i)) < u <= n_i for every i (u = 1 is
@@ -326,9 +327,9 @@ int mertens_sieve_M(uint64_t y1, uint64_t len, int64_t carry, int32_t *M_dev,
  * None of them changes any result -- only speed (Sec. 3 likewise tunes its
  * constants and thresholds for speed alone).
  *   u_factor      automatic sieve limit
- *                 u = u_factor * (count * n)^(2/3) * count^(-1/5),
- *                 clamped to (floor(sqrt(n)), n] (Sec. 2: u = O(n^(2/3)),
- *                 batched u = O((nN)^(2/3)));             default 0.45
+ *                 u = u_factor * g * (count * n)^(2/3), g as in
+ *                 mertens_plan, clamped to (floor(sqrt(n)), n] (Sec. 2:
+ *                 u = O(n^(2/3)), batched u = O((nN)^(2/3))); default 0.45
  *   dense_c       dense cut-off y_c ~ dense_c * sqrt(floor(n/x)) per entry
  *                 (the paper's regions 1/1' bound c1);     default 1.4
  *   gather_scale  multiplies the automatic end of the shared-memory gather

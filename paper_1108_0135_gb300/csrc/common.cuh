@@ -78,14 +78,19 @@ __host__ __device__ __forceinline__ unsigned magic_shift(uint64_t d)
     return bitlen64(d - 1);
 }
 
-// m = floor(2^(63+l)/d) + 1 by restoring long division of the 128-bit
-// numerator 2^(63+l) (high word 2^(l-1), low word 0) by d; the high word is
-// below d, so the quotient fits 64 bits.  d = 1 gives 2^63 + 1.
+// m = floor(2^(63+l)/d) + 1: on the device by restoring long division of the
+// 128-bit numerator 2^(63+l) (high word 2^(l-1), low word 0) by d (the high
+// word is below d, so the quotient fits 64 bits), on the host by one 128-bit
+// division.  d = 1 gives 2^63 + 1.
 __host__ __device__ inline uint64_t magic_of(uint64_t d)
 {
     unsigned l = magic_shift(d);
     if (l == 0)
         return (1ull << 63) + 1ull;
+#ifndef __CUDA_ARCH__
+    // on the host, one 128-by-64 division of 2^(63+l)
+    return (uint64_t)((((unsigned __int128)1) << (63 + l)) / d) + 1ull;
+#endif
     uint64_t r = 1ull << (l - 1);  // running remainder, always < d
     uint64_t q = 0;
     for (int i = 63; i >= 0; --i) {
