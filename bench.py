@@ -566,8 +566,10 @@ def run_native(args, world, rank, local):
             # `value` counts the paper's direct + gathered terms (closed form per
             # entry); the kernels reach the same sums through the mu-form, which
             # executes one quotient per squarefree y below the dense cut-off and
-            # one per gathered j above it:
-            "terms_executed_per_step": SIX_OVER_PI2 * stats["dense_y"] + stats["gather_j"],
+            # one per gathered j above it, less the gathered terms entry 2x takes
+            # from entry x's even j (floor(floor(n/x)/2j) = floor(floor(n/2x)/j)):
+            "terms_executed_per_step": SIX_OVER_PI2 * stats["dense_y"] + stats["gather_j_exec"],
+            "gathered_terms_shared_per_step": stats["gather_j"] - stats["gather_j_exec"],
             "phases_ms": {k: round(v, 3) for k, v in phases.items()},
             "y_sieved_per_s": stats["y_sieved"] * world / (ms_max / 1e3),
             "clocks": clk,
@@ -702,9 +704,11 @@ def rooflines(phases, stats, peaks, nblocks, ipk):
       update_dense: the update's inner step acc += mulhi64(m, 2k) >> l, in
         terms/s.  Algorithmic terms: squarefree y of the dense ranges
         ((6/pi^2) x the summed dense y-range).
-      update_gathered: one term per gathered j, against the faster of that
-        step and the shared-memory gather's float-estimate quotient step
-        (the tile kernel takes the latter, the global path the former).
+      update_gathered: one term per gathered j evaluated (entry 2x takes
+        part of its terms from entry x's even j, so fewer than the method's
+        gathered terms), against the faster of that step and the
+        shared-memory gather's float-estimate quotient step (the tile kernel
+        takes the latter, the global path the former).
       mu_sieve: 32-bit ALU lane operations/s (LOP3 + IADD3 chains).
         Algorithmic operations: one per sieve update (y, p | y or p^2 | y
         for every sieving prime p) plus two per y (decision + scan add).
@@ -718,7 +722,7 @@ def rooflines(phases, stats, peaks, nblocks, ipk):
                      "inner-step probe: LOP3+IADD3 chains on all SMs, 2 ops per pair"),
         "update_dense": (SIX_OVER_PI2 * stats["dense_y"], mulhi_peak, "T mulhi-terms/s",
                          "inner-step probe: acc += mulhi64(m,2k) >> l chains on all SMs"),
-        "update_gathered": (float(stats["gather_j"]), gather_peak, "T terms/s",
+        "update_gathered": (float(stats["gather_j_exec"]), gather_peak, "T terms/s",
                             "inner-step probe: the faster of the mulhi64 step and the "
                             "float-estimate quotient step, chains on all SMs"),
     }

@@ -290,6 +290,11 @@ typedef struct {
     uint64_t h2d_bytes;   /* host-to-device bytes of the plan's inputs      */
     uint64_t d2h_bytes;   /* device-to-host bytes read by mertens_result
                              since the last mertens_run                     */
+    uint64_t gather_j_exec; /* gathered terms evaluated: entry 2x takes the
+                             terms at j' <= floor(jtop_x/2) from entry x's
+                             even j (floor(floor(n/x)/2j') =
+                             floor(floor(n/2x)/j')), so these are fewer
+                             than gather_j                                  */
 } mertens_run_stats;
 
 /* Enables (1) or disables (0) per-phase events for later runs of `plan`

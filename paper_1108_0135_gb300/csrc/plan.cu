@@ -192,6 +192,8 @@ struct mertens_plan_s {
     // device buffers
     PrimeTable pt;
     uint64_t *dK = nullptr, *dJLO = nullptr, *dJC0 = nullptr, *dJCUR = nullptr, *dYCE = nullptr;
+    uint32_t *dEMIT = nullptr;
+    uint64_t gather_j_exec = 0;  // gathered terms evaluated (after sharing)
     uint64_t *dS = nullptr, *dR = nullptr;
     // chunks of the global gather's heavy entries, per block (qcap records)
     uint4 *dqueue = nullptr;
@@ -682,6 +684,40 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
         delete p;
         return MERTENS_ENOTSUP;
     }
+    // ---- gathered terms shared between entries x and 2x ----
+    // floor(floor(n/x)/j) = floor(n/(x j)), so entry 2x's term at j' is entry
+    // x's term at j = 2j'.  Entry x's even j in [JLO_x, JC0_x] are exactly 2j'
+    // for j' in [JLO_2x, floor(JC0_x/2)] (JLO = floor(X/x) + 1 on both sides),
+    // so when floor(JC0_x/2) <= JC0_2x, entry x adds its even-j sum to entry
+    // 2x as well and entry 2x evaluates only j' > floor(JC0_x/2) itself.
+    // Entry x must evaluate its whole range for that, so the sources are the
+    // x with an even number of factors 2 and the receivers the x with an odd
+    // number (both one-word entries of one target).  JOWN replaces JLO on the
+    // device; the host keeps JLO for everything else.
+    std::vector<uint64_t> JOWN(JLO);
+    std::vector<uint32_t> EMIT(K.size(), 0xffffffffu);
+    {
+        const char *e = getenv("MERTENS_SHARE");
+        const bool share = !(e && e[0] == '0');
+        for (size_t i = 0; share && i < count; ++i) {
+            const uint64_t o = p->off[i], X = p->X[i];
+            for (uint64_t x = 1; 2 * x <= X; ++x) {
+                if (__builtin_ctzll(x) & 1)
+                    continue;
+                const size_t e1 = o + x - 1, e2 = o + 2 * x - 1;
+                if (!K[e1] || !K[e2] || JC0[e1] < JLO[e1])
+                    continue;
+                const uint64_t half = JC0[e1] / 2;
+                if (half < JLO[e2] || half > JC0[e2])
+                    continue;
+                EMIT[e1] = (uint32_t)e2;
+                JOWN[e2] = half + 1;
+            }
+        }
+        for (size_t e2 = 0; e2 < K.size(); ++e2)
+            if (K[e2] && JC0[e2] >= JOWN[e2])
+                p->gather_j_exec += JC0[e2] - JOWN[e2] + 1;
+    }
     p->table = table;
     if (table) {
         if (block_len == 0)
@@ -969,6 +1005,7 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
     const size_t E = p->nent;
     p->dK = p->alloc<uint64_t>(E);
     p->dJLO = p->alloc<uint64_t>(E);
+    p->dEMIT = p->alloc<uint32_t>(E);
     p->dJC0 = p->alloc<uint64_t>(E);
     p->dJCUR = p->alloc<uint64_t>(E);
     p->dYCE = p->alloc<uint64_t>(E);
@@ -1053,7 +1090,7 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
     for (auto &a : p->allocs)
         if (!a.first)
             rc = MERTENS_ENOMEM;
-    bool any_null = !p->dK || !p->dJLO || !p->dJC0 || !p->dJCUR || !p->dYCE || !p->dqueue ||
+    bool any_null = !p->dK || !p->dJLO || !p->dEMIT || !p->dJC0 || !p->dJCUR || !p->dYCE || !p->dqueue ||
                     !p->dqlen || !p->dS || !p->dR ||
                     (!table && !p->dmu_aux) ||
                     (p->sieves && (!p->dMloc[0] || !p->dsegsum[0] || !p->dsegoff[0] ||
@@ -1096,7 +1133,8 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
             qs[i].off = p->off[i];
         }
         cudaMemcpy(p->dK, K.data(), E * 8, cudaMemcpyHostToDevice);
-        cudaMemcpy(p->dJLO, JLO.data(), E * 8, cudaMemcpyHostToDevice);
+        cudaMemcpy(p->dJLO, JOWN.data(), E * 8, cudaMemcpyHostToDevice);
+        cudaMemcpy(p->dEMIT, EMIT.data(), E * 4, cudaMemcpyHostToDevice);
         cudaMemcpy(p->dJC0, JC0.data(), E * 8, cudaMemcpyHostToDevice);
         cudaMemcpy(p->dYCE, YCE.data(), E * 8, cudaMemcpyHostToDevice);
         cudaMemcpy(p->dgroups, sg.data(), sg.size() * sizeof(Group), cudaMemcpyHostToDevice);
@@ -1118,7 +1156,7 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
         if (!gitems.empty())
             cudaMemcpy(p->dgitems, gitems.data(), gitems.size() * sizeof(GatherItem),
                        cudaMemcpyHostToDevice);
-        p->h2d_bytes = 4 * E * 8 + sg.size() * sizeof(Group) + items.size() * sizeof(DenseItem) +
+        p->h2d_bytes = 4 * E * 8 + E * 4 + sg.size() * sizeof(Group) + items.size() * sizeof(DenseItem) +
                        count * sizeof(QueryDev) + gtiles.size() * sizeof(GatherTile) +
                        gitems.size() * sizeof(GatherItem) + p->wide.size() * sizeof(WideEntry);
         if (cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming) != cudaSuccess ||
@@ -1393,6 +1431,7 @@ static int run_enqueue(mertens_plan_s *p, cudaStream_t origin, uint64_t *out)
             sa.nent = E;
             sa.K = p->dK;
             sa.JLO = p->dJLO;
+            sa.EMIT = p->dEMIT;
             sa.JC0 = p->dJC0;
             sa.YCE = p->dYCE;
             sa.MG = p->dMG;
@@ -1422,6 +1461,7 @@ static int run_enqueue(mertens_plan_s *p, cudaStream_t origin, uint64_t *out)
                 ga.quot = p->gquot;
                 ga.K = p->dK;
                 ga.JLO = p->dJLO;
+                ga.EMIT = p->dEMIT;
                 ga.JCUR = p->dJCUR;
                 ga.MG = p->dMG;
                 ga.S = p->dS;
@@ -1936,6 +1976,7 @@ int mertens_run_stats_get(mertens_plan_t p, mertens_run_stats *st)
     st->kernels = p->kernels;
     st->dense_y = p->dense_y;
     st->gather_j = p->gather_j;
+    st->gather_j_exec = p->gather_j_exec;
     st->sieve_updates = p->sieve_updates;
     st->h2d_bytes = p->h2d_bytes;
     st->d2h_bytes = p->d2h_bytes;

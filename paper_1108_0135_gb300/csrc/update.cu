@@ -18,6 +18,7 @@
 // Both forms count every j >= floor(k/u)+1 exactly once, so the sum is the
 // same for any yc in [s, floor(k/(floor(k/u)+1)) - 1].
 #include <cstdint>
+#include <type_traits>
 
 #include "common.cuh"
 #include "internal.h"
@@ -217,10 +218,44 @@ __device__ __forceinline__ int64_t block_M(const int64_t *segoff, const int16_t 
     return segoff[i >> kSegShift] + (int64_t)Mloc[i];
 }
 
+// Gathered terms shared between entries x and 2x (one target): since
+// floor(floor(n/x)/j) = floor(n/(x j)), entry x's term at an even j = 2j' is
+// entry 2x's term at j'.  The plan gives entry 2x only the j' above half of
+// entry x's top j (its own range starts there), and entry x adds the sum of
+// its even-j terms to entry 2x as well (EMIT[e] = the index of entry 2x, else
+// kNoEmit).  Results are unchanged; the plan states which entries pair up.
+constexpr uint32_t kNoEmit = 0xffffffffu;
+
+// Warp sum of v where lane l holds terms j = top - l - 32 i (so all of one
+// residue c = (top - l) mod 32): a butterfly over the bits of c from the
+// highest down.  After the steps 16, 8, 4, 2 a lane holds the sum over the
+// lanes of its parity of c, i.e. over the j of its parity; the last step
+// gives the total.  Returns the total; *even = the sum over even j (every
+// lane).
+__device__ __forceinline__ int64_t warp_sum_split2(int64_t v, uint32_t top, uint32_t lane,
+                                                   int64_t *even)
+{
+    const uint32_t c = (top - lane) & 31u;
+#pragma unroll
+    for (uint32_t m = 16u; m >= 2u; m >>= 1)
+        v += __shfl_sync(0xffffffffu, v, (int)((top - (c ^ m)) & 31u));
+    const int64_t other = __shfl_sync(0xffffffffu, v, (int)((top - (c ^ 1u)) & 31u));
+    *even = (c & 1u) ? other : v;
+    return v + other;
+}
+
+// Number of even j in [lo, hi] (1 <= lo <= hi + 1).
+__device__ __forceinline__ uint64_t even_count(uint64_t lo, uint64_t hi)
+{
+    return (hi >> 1) - ((lo - 1u) >> 1);
+}
+
 // M(floor(k/j)) of the block for four j at once: the four magic loads, then
 // the four M loads, so eight loads per lane are in flight instead of a chain.
+// *even gets the part over even j.
 __device__ __forceinline__ int64_t block_M4(const SparseArgs &a, uint64_t k2, uint64_t y1,
-                                            const uint32_t j[4], const bool ok[4])
+                                            const uint32_t j[4], const bool ok[4],
+                                            int64_t *even)
 {
     uint64_t m[4];
 #pragma unroll
@@ -230,11 +265,15 @@ __device__ __forceinline__ int64_t block_M4(const SparseArgs &a, uint64_t k2, ui
 #pragma unroll
     for (int u = 0; u < 4; ++u)
         i[u] = ok[u] ? div_magic(k2, m[u], 32u - __clz(j[u] - 1u)) - y1 : 0ull;
-    int64_t s = 0;
+    int64_t s = 0, se = 0;
 #pragma unroll
     for (int u = 0; u < 4; ++u)
-        if (ok[u])
-            s += block_M(a.segoff, a.Mloc, i[u]);
+        if (ok[u]) {
+            const int64_t v = block_M(a.segoff, a.Mloc, i[u]);
+            s += v;
+            se += (j[u] & 1u) ? 0 : v;
+        }
+    *even += se;
     return s;
 }
 
@@ -263,14 +302,20 @@ __global__ void __launch_bounds__(256) sparse_range_kernel(SparseBlockArgs b, Sp
         jbot = (q2 + 1) > jlo ? (q2 + 1) : jlo;
     }
     const uint64_t cnt = jtop >= jbot ? jtop - jbot + 1 : 0;
-    int64_t add = 0;
+    int64_t add = 0, even = 0;
     if (cnt && cnt <= kLaneTerms) {
         // j < 2^32 here (j <= sqrt(k))
         for (uint32_t j0 = (uint32_t)jbot; j0 <= (uint32_t)jtop; j0 += 4u) {
             const uint32_t j[4] = {j0, j0 + 1u, j0 + 2u, j0 + 3u};
             const bool ok[4] = {true, j0 + 1u <= (uint32_t)jtop, j0 + 2u <= (uint32_t)jtop,
                                 j0 + 3u <= (uint32_t)jtop};
-            add += block_M4(a, k2, b.y1, j, ok);
+            add += block_M4(a, k2, b.y1, j, ok, &even);
+        }
+        if (even_count(jbot, jtop)) {
+            const uint32_t em = a.EMIT[e];
+            if (em != kNoEmit)
+                atomicAdd(reinterpret_cast<unsigned long long *>(a.S + em),
+                          (unsigned long long)even);
         }
     }
     if (k2) {
@@ -325,16 +370,25 @@ __global__ void __launch_bounds__(256) sparse_chunk_kernel(SparseBlockArgs b, Sp
         const uint64_t jt = (uint64_t)r.y | ((uint64_t)r.z << 32);
         const uint32_t n = r.w;  // terms j = jt - n + 1 .. jt; jt <= sqrt(k) < 2^32
         const uint64_t k2 = a.K[e] << 1;
-        int64_t acc = 0;
+        int64_t acc = 0, even = 0;
         for (uint32_t i = lane; i < n; i += 128u) {
             const uint32_t j[4] = {(uint32_t)jt - i, (uint32_t)jt - i - 32u, (uint32_t)jt - i - 64u,
                                    (uint32_t)jt - i - 96u};
             const bool ok[4] = {true, i + 32u < n, i + 64u < n, i + 96u < n};
-            acc += block_M4(a, k2, b.y1, j, ok);
+            acc += block_M4(a, k2, b.y1, j, ok, &even);
         }
-        acc = warp_sum_i64(acc);
-        if (lane == 0)
+        // a lane's j share one residue mod 32: the even part falls out of the
+        // reduction (the per-lane even sum is not needed)
+        acc = warp_sum_split2(acc, (uint32_t)jt, lane, &even);
+        if (lane == 0) {
             atomicAdd(reinterpret_cast<unsigned long long *>(a.S + e), (unsigned long long)acc);
+            if (even_count(jt - n + 1, jt)) {
+                const uint32_t em = a.EMIT[e];
+                if (em != kNoEmit)
+                    atomicAdd(reinterpret_cast<unsigned long long *>(a.S + em),
+                              (unsigned long long)even);
+            }
+        }
     }
 }
 
@@ -401,6 +455,8 @@ __device__ __forceinline__ uint32_t tile_quot(float Rf, float jf, uint64_t R, ui
 template <int kQuot>
 __global__ void __launch_bounds__(512, 3) gather_tile_kernel(GatherArgs a)
 {
+    // running remainders: the 32-bit remainder path keeps only their low word
+    using RT = typename std::conditional<kQuot == kQuotF32, uint32_t, uint64_t>::type;
     extern __shared__ int16_t Mt[];  // kGatherTile
     __shared__ uint32_t s_item;
     __shared__ int64_t s_base;
@@ -474,26 +530,44 @@ __global__ void __launch_bounds__(512, 3) gather_tile_kernel(GatherArgs a)
             const uint32_t t1lo = (uint32_t)T.t1, lim = T.len - 1u;
             // entries with few terms: one lane each, serially
             if (cnt > 0 && cnt <= kLaneTerms) {
-                int acc = 0;
+                // acc: the sum; alt: the alternating sum ending with + on the
+                // last term, so acc + alt (last j even) or acc - alt (odd) is
+                // twice the even-j part
+                int acc = 0, alt = 0;
                 const uint32_t j0 = (uint32_t)jb;
                 if (kQuot == kQuotMagic) {
                     for (uint32_t i = 0; i < cnt; ++i) {
                         const uint32_t j = j0 + i;
                         const uint64_t y = div_magic(k2, a.MG[j], 32u - __clz(j - 1u));
-                        acc += Mt[(uint32_t)y - t1lo];
+                        const int v = Mt[(uint32_t)y - t1lo];
+                        acc += v;
+                        alt = v - alt;
                     }
                 } else {
-                    // R = k - t1 j falls by t1 per step of j
-                    uint64_t R = (k2 >> 1) - T.t1 * (uint64_t)j0;
-                    const float Rf0 = float_of(R), jf0 = float_of(j0), t1f = float_of(T.t1);
+                    // R = k - t1 j falls by t1 per step of j (the 32-bit
+                    // remainder needs only its low word)
+                    const uint64_t R0 = (k2 >> 1) - T.t1 * (uint64_t)j0;
+                    RT R = (RT)R0;
+                    const RT dt = (RT)T.t1;
+                    const float Rf0 = float_of(R0), jf0 = float_of(j0), t1f = float_of(T.t1);
                     float fi = 0.0f;
-                    for (uint32_t i = 0; i < cnt; ++i, R -= T.t1, fi += 1.0f) {
+                    for (uint32_t i = 0; i < cnt; ++i, R -= dt, fi += 1.0f) {
                         const float Rf = __fmaf_rn(fi, -t1f, Rf0), jf = __fadd_rn(jf0, fi);
-                        acc += Mt[tile_quot<kQuot>(Rf, jf, R, j0 + i, lim)];
+                        const int v = Mt[tile_quot<kQuot>(Rf, jf, R, j0 + i, lim)];
+                        acc += v;
+                        alt = v - alt;
                     }
                 }
                 const int64_t tot = (int64_t)acc + (int64_t)cnt * base;
                 atomicAdd(reinterpret_cast<unsigned long long *>(a.S + e), (unsigned long long)tot);
+                const uint32_t jl = j0 + cnt - 1u;
+                const uint32_t ne = (uint32_t)even_count(j0, jl);
+                const uint32_t em = ne ? a.EMIT[e] : kNoEmit;
+                if (em != kNoEmit) {
+                    const int ev = ((jl & 1u) ? acc - alt : acc + alt) >> 1;
+                    atomicAdd(reinterpret_cast<unsigned long long *>(a.S + em),
+                              (unsigned long long)((int64_t)ev + (int64_t)ne * base));
+                }
             }
             // entries with many terms: the whole warp, lanes over j
             uint32_t mask = __ballot_sync(0xffffffffu, cnt > kLaneTerms);
@@ -517,9 +591,11 @@ __global__ void __launch_bounds__(512, 3) gather_tile_kernel(GatherArgs a)
                         }
                     } else {
                         // R = k - t1 j rises by 32 t1 per step, j falls by 32
-                        uint64_t R = (k2s >> 1) - T.t1 * (uint64_t)j;
-                        const uint64_t dR = T.t1 << 5;
-                        const float Rf0 = float_of(R), jf0 = float_of(j), dRf = float_of(dR);
+                        const uint64_t R0 = (k2s >> 1) - T.t1 * (uint64_t)j;
+                        RT R = (RT)R0;
+                        const RT dR = (RT)(T.t1 << 5);
+                        const float Rf0 = float_of(R0), jf0 = float_of(j),
+                                    dRf = float_of(T.t1 << 5);
                         float fi = 0.0f;
                         for (uint32_t i = (uint32_t)lane; i < cns;
                              i += 32u, j -= 32u, R += dR, fi += 1.0f) {
@@ -529,11 +605,19 @@ __global__ void __launch_bounds__(512, 3) gather_tile_kernel(GatherArgs a)
                         }
                     }
                 }
-                int64_t tot = warp_sum_i64((int64_t)acc);
+                // a lane's j share one residue mod 32 (lanes idle past cns
+                // add zero): the even part falls out of the reduction
+                int64_t ev;
+                int64_t tot = warp_sum_split2((int64_t)acc, jts, (uint32_t)lane, &ev);
                 if (lane == 0) {
                     tot += (int64_t)cns * base;
                     atomicAdd(reinterpret_cast<unsigned long long *>(a.S + eb + src),
                               (unsigned long long)tot);
+                    const uint32_t ne = (uint32_t)even_count(jts - cns + 1u, jts);
+                    const uint32_t ems = ne ? a.EMIT[eb + src] : kNoEmit;
+                    if (ems != kNoEmit)
+                        atomicAdd(reinterpret_cast<unsigned long long *>(a.S + ems),
+                                  (unsigned long long)(ev + (int64_t)ne * base));
                 }
             }
         }

@@ -61,6 +61,7 @@ struct SparseArgs {
     uint32_t l_ylo;
     uint32_t qcap;
     const uint64_t *K, *JLO, *JC0, *YCE, *MG;
+    const uint32_t *EMIT;  // entry that also takes the even-j terms (update.cu)
     uint64_t *S;
     uint4 *queue;
     uint32_t *qlen;
@@ -101,6 +102,7 @@ struct GatherArgs {
     const int16_t *Mloc;
     const int64_t *segoff;
     const uint64_t *K, *JLO, *JCUR, *MG;
+    const uint32_t *EMIT;  // entry that also takes the even-j terms (update.cu)
     uint64_t *S;
     uint32_t threads;      // 256 or 512 per CTA
     uint32_t ctas_per_sm;  // 0: as many as fit; else at most this many per SM

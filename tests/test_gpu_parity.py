@@ -242,6 +242,37 @@ def test_gather_quotient_paths(n, u, bl, mode, monkeypatch):
     assert np.array_equal(arr, ref)
 
 
+def _run_arrays(ns, u, bl):
+    plan = pm.mertens_plan(ns, u, bl)
+    try:
+        pm.mertens_run(plan)
+        out = [pm.mertens_result(plan, i, entries=True)[1] for i in range(len(ns))]
+        st = pm.mertens_run_stats_get(plan)
+    finally:
+        pm.mertens_destroy(plan)
+    return out, st
+
+
+@pytest.mark.parametrize("ns,u,bl", [([10**12 + 39], 10**8, 1 << 24),
+                                     ([10**13 + 1], 0, 0),
+                                     ([10**12, 10**12 + 5 * 10**8 + 3, 7 * 10**11 + 1], 0, 1 << 24)])
+def test_shared_even_terms_same_arrays(ns, u, bl, monkeypatch):
+    """Entry 2x takes part of its gathered terms from entry x's even j
+    (floor(floor(n/x)/2j) = floor(floor(n/2x)/j)); the arrays are the same
+    with the sharing switched off (MERTENS_SHARE=0), and fewer terms are
+    evaluated with it."""
+    monkeypatch.setenv("MERTENS_SHARE", "0")
+    off, st_off = _run_arrays(ns, u, bl)
+    monkeypatch.delenv("MERTENS_SHARE")
+    on, st_on = _run_arrays(ns, u, bl)
+    for a, b in zip(off, on):
+        assert np.array_equal(a, b)
+    assert st_off["gather_j_exec"] == st_off["gather_j"] == st_on["gather_j"]
+    assert st_on["gather_j_exec"] < 0.8 * st_on["gather_j"]
+    if ns[0] == 10**12 + 39:
+        assert np.array_equal(on[0], _oracle_array(ns[0], ns[0] // u))
+
+
 def test_batch_same_alone_and_in_mix():
     ns = [10**12 + i * 10**6 + (i * 7919) % 1000 for i in range(8)] + [10**9 + 1, 12345]
     plan = pm.mertens_plan(ns)
@@ -369,14 +400,14 @@ def test_batch_1e17_full_size_alone_equals_batched(batch_1e17, part):
 @pytest.mark.parametrize("i", [1, 63])
 def test_batch_1e17_full_size_entries_against_oracle(batch_1e17, i):
     """Targets 1 and 63: M(n_i) by Table 1's neighbour is not printed, so the
-    entries with the smallest k (about 7e11, the oracle's Sec. 2 recursion at
-    a fraction of a second each) are compared one by one: the last two and
-    six seeded ones with k <= 2e12."""
+    entries with the smallest k (k = floor(n/x) near the batch's u, a few
+    10^12: the oracle's Sec. 2 recursion at about a second each) are compared
+    one by one: the last two and six seeded ones from the last quarter."""
     ns, res, _ = batch_1e17
     n, arr = ns[i], res[i][1]
     X = len(arr)
     rng = np.random.default_rng(1000 + i)
-    xs = [X, X - 1] + [int(v) for v in rng.integers(n // (2 * 10**12), X, size=6)]
+    xs = [X, X - 1] + [int(v) for v in rng.integers(X - X // 4, X, size=6)]
     for x in xs:
         assert arr[x - 1] == oracle.mertens(n // x, L=10**8), (i, x)
 
