@@ -158,7 +158,7 @@ struct mertens_table_s {
     int64_t *segoff = nullptr;
     uint64_t *MG = nullptr, *dl_m = nullptr;
     uint16_t *dl_yo = nullptr;
-    uint32_t *dl_cnt = nullptr;
+    uint2 *dl_cnt = nullptr;
     size_t bytes = 0;
     std::vector<std::pair<void *, size_t>> allocs;
 };

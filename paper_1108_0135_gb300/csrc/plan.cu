@@ -222,7 +222,7 @@ struct mertens_plan_s {
     uint32_t *derr = nullptr, *dcounter = nullptr;
     uint64_t *dMG = nullptr, *ddl_m = nullptr;
     uint16_t *ddl_yo = nullptr;
-    uint32_t *ddl_cnt = nullptr;
+    uint2 *ddl_cnt = nullptr;
     Group *dgroups = nullptr;
     DenseItem *ditems = nullptr;
     uint32_t nitems = 0;
@@ -535,6 +535,8 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
     // ---- per-entry host planning ----
     std::vector<uint64_t> K, JLO, JC0, YCE;
     std::vector<Group> groups;
+    const char *share_env = getenv("MERTENS_SHARE");
+    const bool share_dense = !window && !(share_env && share_env[0] == '0');
     for (size_t i = 0; i < count; ++i) {
         const u128 nn = to_u128(n[i]);
         const uint64_t uu = u.lo ? u.lo : (table ? on_table_u(nn, ub, table->y_max)
@@ -558,19 +560,26 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
             G.first = (uint32_t)(K.size() - 1);
             G.count = 1;
             G.pred = 1;
-            G.pad = 0;
+            G.emit = 0;
             G.yc = 0;
+            G.olo = 0;
+            G.x0 = 1;
+            G.stride = 1;
             groups.push_back(G);
             p->direct.push_back(0);
             p->gathered.push_back(0);
             p->ymax_q.push_back(0);
             continue;
         }
-        std::vector<uint64_t> S_(32), VH(32);
-        std::vector<uint8_t> WD(32);
+        // blocks of 64 consecutive x share a dense cut-off; each is two groups
+        // of 32 (odd x, even x), so the entries x/2 of an even group lie in
+        // one earlier block and share its cut-off (the dense form's sharing)
+        const size_t gstart = groups.size();  // this target's groups: two per block
+        std::vector<uint64_t> S_(64), VH(64);
+        std::vector<uint8_t> WD(64);
         const u128 wide_from = wide_threshold();
-        for (uint64_t x0 = 1; x0 <= X; x0 += 32) {
-            const uint32_t cnt = (uint32_t)std::min<uint64_t>(32, X - x0 + 1);
+        for (uint64_t x0 = 1; x0 <= X; x0 += 64) {
+            const uint32_t cnt = (uint32_t)std::min<uint64_t>(64, X - x0 + 1);
             uint64_t lo = 0, hi = UINT64_MAX, kf = 0;
             bool any_wide = false;
             for (uint32_t t = 0; t < cnt; ++t) {
@@ -625,7 +634,10 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
             Group G;
             G.first = (uint32_t)(K.size() - cnt);
             G.count = cnt;
-            G.pad = 0;
+            G.emit = 0;
+            G.olo = 0;
+            G.x0 = (uint32_t)x0;
+            G.stride = 1;
             if (any_wide) {
                 // per-entry cut-offs; the two-word entries take none
                 G.pred = 1;
@@ -651,7 +663,19 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
                     G.yc = std::max(G.yc, yc);
                 }
             }
-            groups.push_back(G);
+            {
+                // the block as two stride-2 groups (odd x, then even x)
+                Group H = G;
+                H.stride = 2;
+                H.count = (cnt + 1) / 2;
+                groups.push_back(H);
+                if (cnt > 1) {
+                    H.first = G.first + 1;
+                    H.x0 = G.x0 + 1;
+                    H.count = cnt / 2;
+                    groups.push_back(H);
+                }
+            }
             for (uint32_t t = 0; t < cnt; ++t) {
                 const size_t e = G.first + t;
                 if (WD[t]) {
@@ -672,6 +696,41 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
                     p->gather_j += jc0 - JLO[e] + 1;
             }
         }
+        // ---- the dense form's terms shared between entries x and 2x ----
+        // mu(y) floor(floor(n/2x)/y) = -mu(2y) floor(floor(n/x)/2y) for odd y,
+        // and the even squarefree y' <= yc_x are exactly 2y for the odd
+        // squarefree y <= floor(yc_x/2).  So the even group of block M
+        // (x = 64M + 2, ..., whose x/2 = 32M + 1, ... lie in block M/2) leaves
+        // out its odd y <= b = floor(yc/2) of that block's common cut-off when
+        // b is within every one of its entries' cut-offs, and those x/2 add
+        // minus their even-y sums to it.  Not in window plans (their dense
+        // part is cut to the window's y, which 2y can leave).
+        if (share_dense) {
+            const size_t nblk = (X + 63) / 64;
+            for (size_t M = 0; M < nblk; ++M) {
+                const size_t gr = gstart + 2 * M + 1;  // even group of block M
+                if (64 * M + 2 > X || gr >= groups.size())
+                    continue;
+                Group &R = groups[gr];
+                const Group &Sg = groups[gstart + 2 * (M / 2)];
+                if (Sg.pred || Sg.yc < 2)
+                    continue;
+                const uint64_t b = Sg.yc / 2;
+                bool ok = true;
+                for (uint32_t t = 0; t < R.count && ok; ++t) {
+                    const size_t e = (size_t)R.first + 2 * t;
+                    ok = K[e] != 0 && b <= YCE[e];
+                }
+                if (!ok)
+                    continue;
+                R.olo = b;
+                for (uint32_t t = 0; t < R.count; ++t) {
+                    const uint64_t xs = 32 * M + 1 + t;       // source x
+                    const uint64_t o = xs - (64 * (M / 2) + 1);  // offset in its block
+                    groups[gstart + 2 * (M / 2) + (o & 1)].emit |= 1u << (o >> 1);
+                }
+            }
+        }
         p->direct.push_back(d);
         p->gathered.push_back(g);
         p->ymax_q.push_back(ymq);
@@ -684,34 +743,48 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
         delete p;
         return MERTENS_ENOTSUP;
     }
-    // ---- gathered terms shared between entries x and 2x ----
+    // ---- gathered terms shared along chains x, 2x, 4x, 8x, 16x ----
     // floor(floor(n/x)/j) = floor(n/(x j)), so entry 2x's term at j' is entry
-    // x's term at j = 2j'.  Entry x's even j in [JLO_x, JC0_x] are exactly 2j'
-    // for j' in [JLO_2x, floor(JC0_x/2)] (JLO = floor(X/x) + 1 on both sides),
-    // so when floor(JC0_x/2) <= JC0_2x, entry x adds its even-j sum to entry
-    // 2x as well and entry 2x evaluates only j' > floor(JC0_x/2) itself.
-    // Entry x must evaluate its whole range for that, so the sources are the
-    // x with an even number of factors 2 and the receivers the x with an odd
-    // number (both one-word entries of one target).  JOWN replaces JLO on the
-    // device; the host keeps JLO for everything else.
+    // x's term at j = 2j'.  The link x -> 2x (one-word entries of one target)
+    // is valid when h = floor(JC0_x/2) lies in [JLO_2x, JC0_2x]: entry x's
+    // whole range then holds, at its even j, exactly entry 2x's terms
+    // j' in [JLO_2x, h] (JLO = floor(X/x) + 1 on both sides), so entry 2x
+    // evaluates only j' > h itself.  The j' <= h are the terms of x's whole
+    // range, which x and the entries before it in the chain evaluate: each
+    // entry adds the sum of its own terms at j = 0 mod 2^s to entry 2^s x
+    // along valid links.  Chains restart at every x whose power of two is
+    // 0 mod 5 (at most four links, the four levels of the kernels' sums).
+    // JOWN replaces JLO on the device; the host keeps JLO for the rest.
     std::vector<uint64_t> JOWN(JLO);
-    std::vector<uint32_t> EMIT(K.size(), 0xffffffffu);
+    std::vector<uint32_t> EMIT(K.size(), 0u);
     {
         const char *e = getenv("MERTENS_SHARE");
         const bool share = !(e && e[0] == '0');
+        std::vector<uint8_t> link;
         for (size_t i = 0; share && i < count; ++i) {
             const uint64_t o = p->off[i], X = p->X[i];
-            for (uint64_t x = 1; 2 * x <= X; ++x) {
-                if (__builtin_ctzll(x) & 1)
-                    continue;
+            if (X < 2)
+                continue;
+            link.assign(X / 2 + 1, 0);
+            // x < 2^29: EMIT holds x in 29 bits (larger x take no part)
+            for (uint64_t x = 1; 2 * x <= X && x < (1ull << 29); ++x) {
+                if (__builtin_ctzll(2 * x) % (kShareLevels + 1) == 0)
+                    continue;  // 2x starts a chain
                 const size_t e1 = o + x - 1, e2 = o + 2 * x - 1;
-                if (!K[e1] || !K[e2] || JC0[e1] < JLO[e1])
+                if (!K[e1] || !K[e2])
                     continue;
-                const uint64_t half = JC0[e1] / 2;
-                if (half < JLO[e2] || half > JC0[e2])
+                const uint64_t h = JC0[e1] / 2;
+                if (h < JLO[e2] || h > JC0[e2])
                     continue;
-                EMIT[e1] = (uint32_t)e2;
-                JOWN[e2] = half + 1;
+                link[x] = 1;
+                JOWN[e2] = h + 1;
+            }
+            for (uint64_t x = 1; 2 * x <= X && x < (1ull << 29); ++x) {
+                uint32_t L = 0;
+                for (uint64_t y = x; L < kShareLevels && 2 * y <= X && link[y]; y *= 2)
+                    ++L;
+                if (L)
+                    EMIT[o + x - 1] = (uint32_t)x | (L << 29);
             }
         }
         for (size_t e2 = 0; e2 < K.size(); ++e2)
@@ -1069,7 +1142,7 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
             p->dMG = p->alloc<uint64_t>(p->mg_n + 1);
             p->ddl_m = p->alloc<uint64_t>(nchunks * kChunkCapPad);
             p->ddl_yo = p->alloc<uint16_t>(nchunks * kChunkCapPad);
-            p->ddl_cnt = p->alloc<uint32_t>(nchunks);
+            p->ddl_cnt = p->alloc<uint2>(nchunks);
         }
     }
     p->dcarry = p->alloc<int64_t>(p->nblocks + 1);

@@ -87,7 +87,7 @@ int mertens_table_create(mertens_table_t *out, uint64_t y_max, mertens_u128 n_ma
     t->MG = table_alloc<uint64_t>(t, t->mg_n + 1);
     t->dl_m = table_alloc<uint64_t>(t, nchunks * kChunkCapPad);
     t->dl_yo = table_alloc<uint16_t>(t, nchunks * kChunkCapPad);
-    t->dl_cnt = table_alloc<uint32_t>(t, nchunks);
+    t->dl_cnt = table_alloc<uint2>(t, nchunks);
     // scratch of the build
     const uint64_t L = std::min<uint64_t>(1ull << 30, ((y_max + kSegY - 1) / kSegY) * kSegY);
     const uint64_t nblocks = (y_max + L - 1) / L;

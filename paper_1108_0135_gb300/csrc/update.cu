@@ -18,7 +18,6 @@
 // Both forms count every j >= floor(k/u)+1 exactly once, so the sum is the
 // same for any yc in [s, floor(k/(floor(k/u)+1)) - 1].
 #include <cstdint>
-#include <type_traits>
 
 #include "common.cuh"
 #include "internal.h"
@@ -38,49 +37,52 @@ __global__ void magic_table_kernel(uint64_t *__restrict__ MG, uint64_t nd)
 }
 
 // Squarefree list of one chunk of kChunk y values (y <= ydense): the magics
-// of the y with mu = +1, then (from an even index) those with mu = -1, with
-// the offsets y - chunk start, in increasing y.  256 threads x 16 y.
+// and offsets y - chunk start, in increasing y, in four parts -- mu = +1 and
+// odd y, +1 and even y, -1 and odd y, -1 and even y -- each from an even
+// index; dl_cnt = {n0 | n1 << 16, n2 | n3 << 16}.  256 threads x 16 y.
+__device__ __forceinline__ uint32_t even_up(uint32_t v) { return (v + 1u) & ~1u; }
+
 __global__ void __launch_bounds__(256) dense_list_kernel(const int8_t *__restrict__ mu_aux,
                                                          uint64_t ydense,
                                                          const uint64_t *__restrict__ MG,
                                                          uint64_t *__restrict__ dl_m,
                                                          uint16_t *__restrict__ dl_yo,
-                                                         uint32_t *__restrict__ dl_cnt)
+                                                         uint2 *__restrict__ dl_cnt)
 {
     __shared__ uint32_t sh[33];
     const uint64_t c = blockIdx.x;
     const uint64_t cb = c * kChunk;
     int8_t mv[16];
-    uint32_t cp = 0, cm = 0;
+    uint32_t cp = 0, cm = 0;  // per thread: counts of the parts, 16-bit fields (odd | even << 16)
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
         const uint64_t y = cb + threadIdx.x * 16 + k;
         mv[k] = (y >= 1 && y <= ydense) ? mu_aux[y - 1] : (int8_t)0;
-        cp += mv[k] > 0;
-        cm += mv[k] < 0;
+        const uint32_t f = (k & 1) ? 1u : 65536u;  // y even when k is (cb and 16 t are even)
+        cp += mv[k] > 0 ? f : 0u;
+        cm += mv[k] < 0 ? f : 0u;
     }
     uint32_t totp, totm;
-    uint32_t ip = block_scan_u32(cp, sh, &totp);
-    uint32_t im = block_scan_u32(cm, sh, &totm);
-    const uint32_t np_pad = (totp + 1u) & ~1u;
+    const uint32_t ip = block_scan_u32(cp, sh, &totp);  // no field exceeds 2048
+    const uint32_t im = block_scan_u32(cm, sh, &totm);
+    const uint32_t n0 = totp & 0xffffu, n1 = totp >> 16, n2 = totm & 0xffffu;
+    const uint32_t b1 = even_up(n0), b2 = b1 + even_up(n1), b3 = b2 + even_up(n2);
+    uint32_t i0 = ip & 0xffffu, i1 = b1 + (ip >> 16), i2 = b2 + (im & 0xffffu),
+             i3 = b3 + (im >> 16);
     uint64_t *dm = dl_m + c * kChunkCapPad;
     uint16_t *dy = dl_yo + c * kChunkCapPad;
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
         const uint32_t o = threadIdx.x * 16 + k;
         const uint64_t y = cb + o;
-        if (mv[k] > 0) {
-            dm[ip] = MG[y];
-            dy[ip] = (uint16_t)o;
-            ++ip;
-        } else if (mv[k] < 0) {
-            dm[np_pad + im] = MG[y];
-            dy[np_pad + im] = (uint16_t)o;
-            ++im;
+        if (mv[k] != 0) {
+            const uint32_t i = mv[k] > 0 ? ((k & 1) ? i0++ : i1++) : ((k & 1) ? i2++ : i3++);
+            dm[i] = MG[y];
+            dy[i] = (uint16_t)o;
         }
     }
     if (threadIdx.x == 0)
-        dl_cnt[c] = totp | (totm << 16);
+        dl_cnt[c] = make_uint2(totp, totm);
 }
 
 // ---------------------------------------------------------------------------
@@ -120,6 +122,20 @@ __device__ __forceinline__ uint64_t quot_sum_uniform(uint64_t k2, const uint64_t
     return (a0 + a1) + (a2 + a3);
 }
 
+// The same over mp[s0 .. s0 + n): a first odd element alone, then from an
+// even index (mp itself starts at an even index).
+__device__ __forceinline__ uint64_t quot_sum_uniform_at(uint64_t k2, const uint64_t *mp,
+                                                        uint32_t s0, uint32_t n, unsigned l)
+{
+    uint64_t a = 0;
+    if ((s0 & 1u) && n) {
+        a = div_magic(k2, mp[s0], l);
+        ++s0;
+        --n;
+    }
+    return a + quot_sum_uniform(k2, mp + s0, n, l);
+}
+
 // Same with a per-term shift (chunk 0) and/or a per-lane cut-off y <= ycl.
 __device__ __forceinline__ uint64_t quot_sum_general(uint64_t k2, const uint64_t *mp,
                                                      const uint16_t *yp, uint32_t n, uint64_t cb,
@@ -141,7 +157,7 @@ __global__ void __launch_bounds__(kDenseThreads) dense_update_kernel(DenseArgs a
     uint64_t *s_m = reinterpret_cast<uint64_t *>(smem);
     uint16_t *s_yo = reinterpret_cast<uint16_t *>(s_m + kDenseChunks * kChunkCapPad);
     __shared__ uint32_t s_item;
-    __shared__ uint32_t s_cnt[kDenseChunks];
+    __shared__ uint2 s_cnt[kDenseChunks];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     for (;;) {
         if (threadIdx.x == 0)
@@ -152,8 +168,9 @@ __global__ void __launch_bounds__(kDenseThreads) dense_update_kernel(DenseArgs a
             break;
         const DenseItem d = a.items[it];
         for (uint32_t c = d.c0; c < d.c1; ++c) {
-            const uint32_t cnt = a.dl_cnt[c];
-            const uint32_t tot = (((cnt & 0xffffu) + 1u) & ~1u) + (cnt >> 16);
+            const uint2 cnt = a.dl_cnt[c];
+            const uint32_t tot = even_up(cnt.x & 0xffffu) + even_up(cnt.x >> 16) +
+                                 even_up(cnt.y & 0xffffu) + (cnt.y >> 16);
             const uint64_t *src = a.dl_m + (uint64_t)c * kChunkCapPad;
             const uint16_t *ysrc = a.dl_yo + (uint64_t)c * kChunkCapPad;
             uint64_t *dst = s_m + (c - d.c0) * kChunkCapPad;
@@ -169,36 +186,66 @@ __global__ void __launch_bounds__(kDenseThreads) dense_update_kernel(DenseArgs a
         for (uint32_t g = d.g0 + warp; g < d.g1; g += nwarp) {
             const Group G = a.groups[g];
             const bool act = (uint32_t)lane < G.count;
-            const uint64_t e = (uint64_t)G.first + lane;
+            const uint64_t e = (uint64_t)G.first + (uint64_t)G.stride * lane;
             const uint64_t k2 = act ? (a.K[e] << 1) : 0ull;
             const uint64_t ycl = G.pred ? (act ? a.YCE[e] : 0ull) : G.yc;
-            uint64_t accp = 0, accm = 0;
+            uint64_t acc_o = 0, acc_e = 0;  // odd-y and even-y parts, mod 2^64
             for (uint32_t c = d.c0; c < d.c1; ++c) {
                 const uint64_t cb = (uint64_t)c * kChunk;
                 if (cb > G.yc)
                     break;
-                const uint32_t cnt = s_cnt[c - d.c0];
-                uint32_t np = cnt & 0xffffu, nm = cnt >> 16;
-                const uint32_t npad = (np + 1u) & ~1u;
+                const uint2 cnt = s_cnt[c - d.c0];
+                // parts: [lo, hi) index ranges of +odd, +even, -odd, -even
+                uint32_t n[4] = {cnt.x & 0xffffu, cnt.x >> 16, cnt.y & 0xffffu, cnt.y >> 16};
+                uint32_t base[4];
+                base[0] = 0;
+                base[1] = even_up(n[0]);
+                base[2] = base[1] + even_up(n[1]);
+                base[3] = base[2] + even_up(n[2]);
                 const uint64_t *mp = s_m + (c - d.c0) * kChunkCapPad;
                 const uint16_t *yp = s_yo + (c - d.c0) * kChunkCapPad;
                 if (cb + kChunk - 1 > G.yc) {
                     const uint32_t lim = (uint32_t)(G.yc - cb);
-                    np = upper_bound_u16(yp, np, lim);
-                    nm = upper_bound_u16(yp + npad, nm, lim);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        n[q] = upper_bound_u16(yp + base[q], n[q], lim);
+                }
+                // odd y <= olo come from entry x/2 (the group's lower bound)
+                uint32_t skip[4] = {0, 0, 0, 0};
+                if (G.olo >= cb) {
+                    if (G.olo >= cb + kChunk - 1) {
+                        skip[0] = n[0];
+                        skip[2] = n[2];
+                    } else {
+                        const uint32_t lo = (uint32_t)(G.olo - cb);
+                        skip[0] = upper_bound_u16(yp + base[0], n[0], lo);
+                        skip[2] = upper_bound_u16(yp + base[2], n[2], lo);
+                    }
                 }
                 const unsigned l = magic_shift((c + 1) * (uint64_t)kChunk - 1);
-                if (c == 0 || G.pred) {
-                    accp += quot_sum_general(k2, mp, yp, np, cb, l, c == 0, ycl);
-                    accm += quot_sum_general(k2, mp + npad, yp + npad, nm, cb, l, c == 0, ycl);
-                } else {
-                    accp += quot_sum_uniform(k2, mp, np, l);
-                    accm += quot_sum_uniform(k2, mp + npad, nm, l);
+                uint64_t part[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint32_t s0 = skip[q], cntq = n[q] > s0 ? n[q] - s0 : 0u;
+                    if (c == 0 || G.pred)
+                        part[q] = quot_sum_general(k2, mp + base[q] + s0, yp + base[q] + s0, cntq,
+                                                   cb, l, c == 0, ycl);
+                    else
+                        part[q] = quot_sum_uniform_at(k2, mp + base[q], s0, cntq, l);
+                }
+                acc_o += part[0] - part[2];
+                acc_e += part[1] - part[3];
+            }
+            if (act) {
+                atomicAdd(reinterpret_cast<unsigned long long *>(a.S + e),
+                          (unsigned long long)(acc_o + acc_e));
+                if ((G.emit >> lane) & 1u) {
+                    // entry 2x: its odd y' = y/2 terms are minus these
+                    const uint64_t x = (uint64_t)G.x0 + (uint64_t)G.stride * lane;
+                    atomicAdd(reinterpret_cast<unsigned long long *>(a.S + e + x),
+                              (unsigned long long)(0ull - acc_e));
                 }
             }
-            if (act)
-                atomicAdd(reinterpret_cast<unsigned long long *>(a.S + e),
-                          (unsigned long long)(accp - accm));
         }
         __syncthreads();
     }
@@ -218,44 +265,62 @@ __device__ __forceinline__ int64_t block_M(const int64_t *segoff, const int16_t 
     return segoff[i >> kSegShift] + (int64_t)Mloc[i];
 }
 
-// Gathered terms shared between entries x and 2x (one target): since
-// floor(floor(n/x)/j) = floor(n/(x j)), entry x's term at an even j = 2j' is
-// entry 2x's term at j'.  The plan gives entry 2x only the j' above half of
-// entry x's top j (its own range starts there), and entry x adds the sum of
-// its even-j terms to entry 2x as well (EMIT[e] = the index of entry 2x, else
-// kNoEmit).  Results are unchanged; the plan states which entries pair up.
-constexpr uint32_t kNoEmit = 0xffffffffu;
+// Gathered terms shared along chains x, 2x, 4x, 8x, 16x of one target:
+// since floor(floor(n/x)/(2^s j')) = floor(floor(n/(2^s x))/j'), entry x's
+// term at j = 2^s j' is entry 2^s x's term at j'.  The plan gives each entry
+// of a chain after its first only the j above half of the previous entry's
+// top (its own range starts there; the part below is the previous entries'
+// terms), and every entry adds, for s = 1 .. L, the sum of its own terms at
+// j = 0 mod 2^s to entry 2^s x.  EMIT[e] = x | L << 29 (L <= 4; 0: none).
+// Results are unchanged; the plan states which chains are valid.
+static_assert(kShareLevels >= 1 && kShareLevels <= 4, "level sums come from the c-bit butterfly");
+constexpr uint32_t kShareShift = 29;
 
 // Warp sum of v where lane l holds terms j = top - l - 32 i (so all of one
 // residue c = (top - l) mod 32): a butterfly over the bits of c from the
-// highest down.  After the steps 16, 8, 4, 2 a lane holds the sum over the
-// lanes of its parity of c, i.e. over the j of its parity; the last step
-// gives the total.  Returns the total; *even = the sum over even j (every
-// lane).
-__device__ __forceinline__ int64_t warp_sum_split2(int64_t v, uint32_t top, uint32_t lane,
-                                                   int64_t *even)
+// highest down.  After the step on bit 2^s every lane holds the sum over the
+// c' that agree with its c below bit s, so the lane with c = 0 holds the sum
+// over j = 0 mod 2^s: h[s - 1] (s = 4 .. 1, valid in that lane only).  The
+// last step gives the total (every lane).
+__device__ __forceinline__ int64_t warp_sum_levels(int64_t v, uint32_t top, uint32_t lane,
+                                                   int64_t h[kShareLevels])
 {
     const uint32_t c = (top - lane) & 31u;
 #pragma unroll
-    for (uint32_t m = 16u; m >= 2u; m >>= 1)
-        v += __shfl_sync(0xffffffffu, v, (int)((top - (c ^ m)) & 31u));
-    const int64_t other = __shfl_sync(0xffffffffu, v, (int)((top - (c ^ 1u)) & 31u));
-    *even = (c & 1u) ? other : v;
-    return v + other;
+    for (int s = 4; s >= 1; --s) {
+        v += __shfl_sync(0xffffffffu, v, (int)((top - (c ^ (1u << s))) & 31u));
+        if (s <= (int)kShareLevels)
+            h[s - 1] = v;
+    }
+    return v + __shfl_sync(0xffffffffu, v, (int)((top - (c ^ 1u)) & 31u));
 }
 
-// Number of even j in [lo, hi] (1 <= lo <= hi + 1).
-__device__ __forceinline__ uint64_t even_count(uint64_t lo, uint64_t hi)
+// Adds entry e's level sums over its own j in [lo, hi] (1 <= lo) to the
+// entries 2^s x it feeds; base is added once per term (the tile kernels'
+// staged values are relative to it).
+__device__ __forceinline__ void emit_levels(uint64_t *S, uint64_t e, uint32_t em, uint64_t lo,
+                                            uint64_t hi, const int64_t h[kShareLevels],
+                                            int64_t base)
 {
-    return (hi >> 1) - ((lo - 1u) >> 1);
+    const uint32_t L = em >> kShareShift;
+    const uint64_t x = em & ((1u << kShareShift) - 1u);
+#pragma unroll
+    for (uint32_t s = 1; s <= kShareLevels; ++s) {
+        if (s > L)
+            break;
+        const uint64_t c = (hi >> s) - ((lo - 1u) >> s);  // multiples of 2^s in [lo, hi]
+        if (c)
+            atomicAdd(reinterpret_cast<unsigned long long *>(S + e + ((1ull << s) - 1u) * x),
+                      (unsigned long long)(h[s - 1] + (int64_t)c * base));
+    }
 }
 
 // M(floor(k/j)) of the block for four j at once: the four magic loads, then
 // the four M loads, so eight loads per lane are in flight instead of a chain.
-// *even gets the part over even j.
+// h[s - 1] gets the part over j = 0 mod 2^s.
 __device__ __forceinline__ int64_t block_M4(const SparseArgs &a, uint64_t k2, uint64_t y1,
                                             const uint32_t j[4], const bool ok[4],
-                                            int64_t *even)
+                                            int64_t h[kShareLevels])
 {
     uint64_t m[4];
 #pragma unroll
@@ -265,15 +330,16 @@ __device__ __forceinline__ int64_t block_M4(const SparseArgs &a, uint64_t k2, ui
 #pragma unroll
     for (int u = 0; u < 4; ++u)
         i[u] = ok[u] ? div_magic(k2, m[u], 32u - __clz(j[u] - 1u)) - y1 : 0ull;
-    int64_t s = 0, se = 0;
+    int64_t s = 0;
 #pragma unroll
     for (int u = 0; u < 4; ++u)
         if (ok[u]) {
             const int64_t v = block_M(a.segoff, a.Mloc, i[u]);
             s += v;
-            se += (j[u] & 1u) ? 0 : v;
+#pragma unroll
+            for (uint32_t l = 0; l < kShareLevels; ++l)
+                h[l] += (j[u] & ((2u << l) - 1u)) ? 0 : v;
         }
-    *even += se;
     return s;
 }
 
@@ -302,20 +368,20 @@ __global__ void __launch_bounds__(256) sparse_range_kernel(SparseBlockArgs b, Sp
         jbot = (q2 + 1) > jlo ? (q2 + 1) : jlo;
     }
     const uint64_t cnt = jtop >= jbot ? jtop - jbot + 1 : 0;
-    int64_t add = 0, even = 0;
+    int64_t add = 0;
     if (cnt && cnt <= kLaneTerms) {
         // j < 2^32 here (j <= sqrt(k))
+        int64_t h[kShareLevels] = {};
         for (uint32_t j0 = (uint32_t)jbot; j0 <= (uint32_t)jtop; j0 += 4u) {
             const uint32_t j[4] = {j0, j0 + 1u, j0 + 2u, j0 + 3u};
             const bool ok[4] = {true, j0 + 1u <= (uint32_t)jtop, j0 + 2u <= (uint32_t)jtop,
                                 j0 + 3u <= (uint32_t)jtop};
-            add += block_M4(a, k2, b.y1, j, ok, &even);
+            add += block_M4(a, k2, b.y1, j, ok, h);
         }
-        if (even_count(jbot, jtop)) {
+        if (jtop >= 2u) {
             const uint32_t em = a.EMIT[e];
-            if (em != kNoEmit)
-                atomicAdd(reinterpret_cast<unsigned long long *>(a.S + em),
-                          (unsigned long long)even);
+            if (em)
+                emit_levels(a.S, e, em, jbot, jtop, h, 0);
         }
     }
     if (k2) {
@@ -370,24 +436,21 @@ __global__ void __launch_bounds__(256) sparse_chunk_kernel(SparseBlockArgs b, Sp
         const uint64_t jt = (uint64_t)r.y | ((uint64_t)r.z << 32);
         const uint32_t n = r.w;  // terms j = jt - n + 1 .. jt; jt <= sqrt(k) < 2^32
         const uint64_t k2 = a.K[e] << 1;
-        int64_t acc = 0, even = 0;
+        int64_t acc = 0, h[kShareLevels] = {};
         for (uint32_t i = lane; i < n; i += 128u) {
             const uint32_t j[4] = {(uint32_t)jt - i, (uint32_t)jt - i - 32u, (uint32_t)jt - i - 64u,
                                    (uint32_t)jt - i - 96u};
             const bool ok[4] = {true, i + 32u < n, i + 64u < n, i + 96u < n};
-            acc += block_M4(a, k2, b.y1, j, ok, &even);
+            acc += block_M4(a, k2, b.y1, j, ok, h);
         }
-        // a lane's j share one residue mod 32: the even part falls out of the
-        // reduction (the per-lane even sum is not needed)
-        acc = warp_sum_split2(acc, (uint32_t)jt, lane, &even);
-        if (lane == 0) {
+        // a lane's j share one residue mod 32: the level sums fall out of the
+        // reduction (the per-lane ones are not needed)
+        acc = warp_sum_levels(acc, (uint32_t)jt, lane, h);
+        if (lane == ((uint32_t)jt & 31u)) {
             atomicAdd(reinterpret_cast<unsigned long long *>(a.S + e), (unsigned long long)acc);
-            if (even_count(jt - n + 1, jt)) {
-                const uint32_t em = a.EMIT[e];
-                if (em != kNoEmit)
-                    atomicAdd(reinterpret_cast<unsigned long long *>(a.S + em),
-                              (unsigned long long)even);
-            }
+            const uint32_t em = a.EMIT[e];
+            if (em)
+                emit_levels(a.S, e, em, jt - n + 1, jt, h, 0);
         }
     }
 }
@@ -442,6 +505,73 @@ __device__ __forceinline__ uint32_t tile_quot(float Rf, float jf, uint64_t R, ui
     return q < lim ? q : lim;
 }
 
+// The lane-per-entry part of the tile kernel: entry e's cnt (<= kLaneTerms)
+// terms j = j0 .. j0 + cnt - 1 in the staged tile, one lane, and its level
+// sums for the entries 2^s x it feeds.
+template <int kQuot>
+__device__ __forceinline__ void tile_lane_entry(uint64_t *S, const uint32_t *EMIT, const uint64_t *MG,
+                                             uint64_t t1, uint32_t lim, int64_t base, uint32_t e,
+                                             uint64_t k2, uint32_t j0, uint32_t cnt)
+{
+    extern __shared__ int16_t Mt[];
+    // acc: the sum; h[s - 1]: the part over j = 0 mod 2^s (for the entries
+    // 2^s x this one feeds)
+    int acc = 0, h[kShareLevels] = {};
+    if (kQuot == kQuotMagic) {
+        const uint32_t t1lo = (uint32_t)t1;
+        for (uint32_t i = 0; i < cnt; ++i) {
+            const uint32_t j = j0 + i;
+            const uint64_t y = div_magic(k2, MG[j], 32u - __clz(j - 1u));
+            const int v = Mt[(uint32_t)y - t1lo];
+            acc += v;
+#pragma unroll
+            for (uint32_t l = 0; l < kShareLevels; ++l)
+                h[l] += (j & ((2u << l) - 1u)) ? 0 : v;
+        }
+    } else {
+        // R = k - t1 j falls by t1 per step of j
+        uint64_t R = (k2 >> 1) - t1 * (uint64_t)j0;
+        const float Rf0 = float_of(R), jf0 = float_of(j0), t1f = float_of(t1);
+        float fi = 0.0f;
+        for (uint32_t i = 0; i < cnt; ++i, R -= t1, fi += 1.0f) {
+            const float Rf = __fmaf_rn(fi, -t1f, Rf0), jf = __fadd_rn(jf0, fi);
+            const uint32_t j = j0 + i;
+            const int v = Mt[tile_quot<kQuot>(Rf, jf, R, j, lim)];
+            acc += v;
+#pragma unroll
+            for (uint32_t l = 0; l < kShareLevels; ++l)
+                h[l] += (j & ((2u << l) - 1u)) ? 0 : v;
+        }
+    }
+    atomicAdd(reinterpret_cast<unsigned long long *>(S + e),
+              (unsigned long long)((int64_t)acc + (int64_t)cnt * base));
+    const uint32_t jl = j0 + cnt - 1u;
+    const uint32_t em = jl >= 2u ? EMIT[e] : 0u;
+    if (em) {
+        int64_t hl[kShareLevels];
+#pragma unroll
+        for (uint32_t l = 0; l < kShareLevels; ++l)
+            hl[l] = h[l];
+        emit_levels(S, e, em, j0, jl, hl, base);
+    }
+}
+
+// The end of the warp-per-entry loop for an entry that feeds entries 2^s x:
+// a lane's j share one residue mod 32 (lanes idle past cns add zero), so the
+// level sums fall out of the reduction in the lane whose j are 0 mod 32.
+__device__ __forceinline__ void tile_warp_emit(uint64_t *S, uint32_t e, uint32_t em, int64_t acc,
+                                            uint32_t jts, uint32_t cns, uint32_t lane,
+                                            int64_t base)
+{
+    int64_t h[kShareLevels];
+    const int64_t tot = warp_sum_levels(acc, jts, lane, h);
+    if (lane == (jts & 31u)) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(S + e),
+                  (unsigned long long)(tot + (int64_t)cns * base));
+        emit_levels(S, e, em, jts - cns + 1u, jts, h, base);
+    }
+}
+
 // Shared-memory gather path for the low, dense part of a block.  A work item
 // is one tile [t1, t1+len) of y and a range of entries of one target.  The
 // tile's M(y) - M(t1-1) is staged in shared memory as int16 (|value| <= 3/4
@@ -455,8 +585,6 @@ __device__ __forceinline__ uint32_t tile_quot(float Rf, float jf, uint64_t R, ui
 template <int kQuot>
 __global__ void __launch_bounds__(512, 3) gather_tile_kernel(GatherArgs a)
 {
-    // running remainders: the 32-bit remainder path keeps only their low word
-    using RT = typename std::conditional<kQuot == kQuotF32, uint32_t, uint64_t>::type;
     extern __shared__ int16_t Mt[];  // kGatherTile
     __shared__ uint32_t s_item;
     __shared__ int64_t s_base;
@@ -529,46 +657,9 @@ __global__ void __launch_bounds__(512, 3) gather_tile_kernel(GatherArgs a)
             const uint32_t cnt = jt >= jb ? (uint32_t)(jt - jb + 1) : 0u;
             const uint32_t t1lo = (uint32_t)T.t1, lim = T.len - 1u;
             // entries with few terms: one lane each, serially
-            if (cnt > 0 && cnt <= kLaneTerms) {
-                // acc: the sum; alt: the alternating sum ending with + on the
-                // last term, so acc + alt (last j even) or acc - alt (odd) is
-                // twice the even-j part
-                int acc = 0, alt = 0;
-                const uint32_t j0 = (uint32_t)jb;
-                if (kQuot == kQuotMagic) {
-                    for (uint32_t i = 0; i < cnt; ++i) {
-                        const uint32_t j = j0 + i;
-                        const uint64_t y = div_magic(k2, a.MG[j], 32u - __clz(j - 1u));
-                        const int v = Mt[(uint32_t)y - t1lo];
-                        acc += v;
-                        alt = v - alt;
-                    }
-                } else {
-                    // R = k - t1 j falls by t1 per step of j (the 32-bit
-                    // remainder needs only its low word)
-                    const uint64_t R0 = (k2 >> 1) - T.t1 * (uint64_t)j0;
-                    RT R = (RT)R0;
-                    const RT dt = (RT)T.t1;
-                    const float Rf0 = float_of(R0), jf0 = float_of(j0), t1f = float_of(T.t1);
-                    float fi = 0.0f;
-                    for (uint32_t i = 0; i < cnt; ++i, R -= dt, fi += 1.0f) {
-                        const float Rf = __fmaf_rn(fi, -t1f, Rf0), jf = __fadd_rn(jf0, fi);
-                        const int v = Mt[tile_quot<kQuot>(Rf, jf, R, j0 + i, lim)];
-                        acc += v;
-                        alt = v - alt;
-                    }
-                }
-                const int64_t tot = (int64_t)acc + (int64_t)cnt * base;
-                atomicAdd(reinterpret_cast<unsigned long long *>(a.S + e), (unsigned long long)tot);
-                const uint32_t jl = j0 + cnt - 1u;
-                const uint32_t ne = (uint32_t)even_count(j0, jl);
-                const uint32_t em = ne ? a.EMIT[e] : kNoEmit;
-                if (em != kNoEmit) {
-                    const int ev = ((jl & 1u) ? acc - alt : acc + alt) >> 1;
-                    atomicAdd(reinterpret_cast<unsigned long long *>(a.S + em),
-                              (unsigned long long)((int64_t)ev + (int64_t)ne * base));
-                }
-            }
+            if (cnt > 0 && cnt <= kLaneTerms)
+                tile_lane_entry<kQuot>(a.S, a.EMIT, a.MG, T.t1, lim, base, e, k2, (uint32_t)jb,
+                                       cnt);
             // entries with many terms: the whole warp, lanes over j
             uint32_t mask = __ballot_sync(0xffffffffu, cnt > kLaneTerms);
             while (mask) {
@@ -591,11 +682,9 @@ __global__ void __launch_bounds__(512, 3) gather_tile_kernel(GatherArgs a)
                         }
                     } else {
                         // R = k - t1 j rises by 32 t1 per step, j falls by 32
-                        const uint64_t R0 = (k2s >> 1) - T.t1 * (uint64_t)j;
-                        RT R = (RT)R0;
-                        const RT dR = (RT)(T.t1 << 5);
-                        const float Rf0 = float_of(R0), jf0 = float_of(j),
-                                    dRf = float_of(T.t1 << 5);
+                        uint64_t R = (k2s >> 1) - T.t1 * (uint64_t)j;
+                        const uint64_t dR = T.t1 << 5;
+                        const float Rf0 = float_of(R), jf0 = float_of(j), dRf = float_of(dR);
                         float fi = 0.0f;
                         for (uint32_t i = (uint32_t)lane; i < cns;
                              i += 32u, j -= 32u, R += dR, fi += 1.0f) {
@@ -605,19 +694,17 @@ __global__ void __launch_bounds__(512, 3) gather_tile_kernel(GatherArgs a)
                         }
                     }
                 }
-                // a lane's j share one residue mod 32 (lanes idle past cns
-                // add zero): the even part falls out of the reduction
-                int64_t ev;
-                int64_t tot = warp_sum_split2((int64_t)acc, jts, (uint32_t)lane, &ev);
-                if (lane == 0) {
-                    tot += (int64_t)cns * base;
-                    atomicAdd(reinterpret_cast<unsigned long long *>(a.S + eb + src),
-                              (unsigned long long)tot);
-                    const uint32_t ne = (uint32_t)even_count(jts - cns + 1u, jts);
-                    const uint32_t ems = ne ? a.EMIT[eb + src] : kNoEmit;
-                    if (ems != kNoEmit)
-                        atomicAdd(reinterpret_cast<unsigned long long *>(a.S + ems),
-                                  (unsigned long long)(ev + (int64_t)ne * base));
+                // the entry's sum; if it feeds entries 2^s x, also its level
+                // sums (tile_warp_emit)
+                const uint32_t ems = a.EMIT[eb + src];  // one address: warp-uniform
+                if (ems) {
+                    tile_warp_emit(a.S, eb + src, ems, (int64_t)acc, jts, cns, (uint32_t)lane,
+                                   base);
+                } else {
+                    const int64_t tot = warp_sum_i64((int64_t)acc);
+                    if (lane == 0)
+                        atomicAdd(reinterpret_cast<unsigned long long *>(a.S + eb + src),
+                                  (unsigned long long)(tot + (int64_t)cns * base));
                 }
             }
         }
@@ -789,7 +876,7 @@ int magic_table_enqueue(uint64_t *MG, uint64_t nd, cudaStream_t s)
 }
 
 int dense_list_enqueue(const int8_t *mu_aux, uint64_t ydense, const uint64_t *MG, uint64_t *dl_m,
-                       uint16_t *dl_yo, uint32_t *dl_cnt, cudaStream_t s)
+                       uint16_t *dl_yo, uint2 *dl_cnt, cudaStream_t s)
 {
     const uint64_t nchunks = ydense / kChunk + 1;
     dense_list_kernel<<<(unsigned)nchunks, 256, 0, s>>>(mu_aux, ydense, MG, dl_m, dl_yo, dl_cnt);

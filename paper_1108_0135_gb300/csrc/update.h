@@ -7,20 +7,31 @@
 namespace mert {
 
 // Chunks staged per dense work item, threads per dense CTA, and the padded
-// per-chunk capacity of the squarefree list (the mu = -1 part starts at an
-// even index so that both parts can be read 16 bytes at a time).
+// per-chunk capacity of the squarefree list (four parts -- mu = +1 odd y,
+// +1 even, -1 odd, -1 even -- each starting at an even index so that they
+// can be read 16 bytes at a time; at most 3072 squarefree y per chunk).
 constexpr int kDenseChunks = 2;
 constexpr int kDenseThreads = 256;
-constexpr int kChunkCapPad = 3074;
+constexpr int kChunkCapPad = 3076;
 
-// 32 consecutive entries of one target sharing one dense cut-off yc (pred =
-// 0), or with a cut-off per entry in YCE (pred = 1; yc = their maximum).
+// Gathered terms are shared along chains x, 2x, ..., 2^kShareLevels x of
+// one target (update.cu): the level sums the kernels produce per entry.
+constexpr uint32_t kShareLevels = 4;
+
+// Up to 32 entries of one target, e = first + stride * lane (x = x0 +
+// stride * lane), sharing one dense cut-off yc (pred = 0), or with a cut-off
+// per entry in YCE (pred = 1; yc = their maximum).  Odd y <= olo are left
+// out of their sums (0: none): those terms come from the entries x/2, whose
+// lanes in `emit` add minus their even-y sums to entry 2x (update.cu).
 struct Group {
-    uint32_t first;  // global index of the first entry
-    uint32_t count;  // entries in the group (1..32)
+    uint32_t first;
+    uint32_t count;   // entries in the group (1..32)
     uint32_t pred;
-    uint32_t pad;
+    uint32_t emit;    // lanes that add their even-y sum to entry 2x
     uint64_t yc;
+    uint64_t olo;
+    uint32_t x0;
+    uint32_t stride;  // 1 or 2
 };
 
 // Dense work item: chunks [c0, c1) for the groups [g0, g1) of the sorted
@@ -38,7 +49,7 @@ struct DenseArgs {
     const uint64_t *YCE;  // dense cut-off per entry
     const uint64_t *dl_m;
     const uint16_t *dl_yo;
-    const uint32_t *dl_cnt;
+    const uint2 *dl_cnt;
     uint64_t *S;
     uint32_t ctas_per_sm;  // 0: as many as fit; else at most this many per SM
 };
@@ -61,7 +72,7 @@ struct SparseArgs {
     uint32_t l_ylo;
     uint32_t qcap;
     const uint64_t *K, *JLO, *JC0, *YCE, *MG;
-    const uint32_t *EMIT;  // entry that also takes the even-j terms (update.cu)
+    const uint32_t *EMIT;  // x | L << 29: the entries 2^s x (s <= L) it feeds (update.cu)
     uint64_t *S;
     uint4 *queue;
     uint32_t *qlen;
@@ -102,7 +113,7 @@ struct GatherArgs {
     const int16_t *Mloc;
     const int64_t *segoff;
     const uint64_t *K, *JLO, *JCUR, *MG;
-    const uint32_t *EMIT;  // entry that also takes the even-j terms (update.cu)
+    const uint32_t *EMIT;  // x | L << 29: the entries 2^s x (s <= L) it feeds (update.cu)
     uint64_t *S;
     uint32_t threads;      // 256 or 512 per CTA
     uint32_t ctas_per_sm;  // 0: as many as fit; else at most this many per SM
@@ -161,7 +172,7 @@ int carry_from_table_enqueue(const int16_t *Mloc, const int64_t *segoff, uint64_
                              int64_t *out, cudaStream_t s);
 int wide_update_enqueue(const WideArgs &a, uint32_t nw, uint32_t grid_x, cudaStream_t s);
 int dense_list_enqueue(const int8_t *mu_aux, uint64_t ydense, const uint64_t *MG, uint64_t *dl_m,
-                       uint16_t *dl_yo, uint32_t *dl_cnt, cudaStream_t s);
+                       uint16_t *dl_yo, uint2 *dl_cnt, cudaStream_t s);
 int dense_update_enqueue(const DenseArgs &a, cudaStream_t s);
 int sparse_block_enqueue(const SparseBlockArgs &b, const SparseArgs &a, cudaStream_t s);
 int gather_tiles_enqueue(const GatherArgs &a, cudaStream_t s);
