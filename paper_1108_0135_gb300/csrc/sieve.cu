@@ -637,10 +637,10 @@ __global__ void __launch_bounds__(kSieveThreads, 1) mu_sieve_byte_kernel(ByteArg
 // Work of a tile:
 //   * the pre-sieve pattern: primes 2, 3, 5, 7 with the base 1 and the flags
 //     of 4, 9, 25, 49 (period 44100, one bulk asynchronous copy);
-//   * primes 11 <= p < 512: a warp over the multiples of one prime, largest
+//   * primes 11 <= p < 1024: a warp over the multiples of one prime, largest
 //     jobs first;
-//   * primes p >= 512: a lane per prime, two per lane, the hits of primes
-//     below a ninth of the tile four at a time with loop-invariant shifted
+//   * primes p >= 1024: a lane per prime, four per lane, the hits of primes
+//     below a third of the tile four at a time with loop-invariant shifted
 //     weights; the square of a prime below 8192 per lane, those of larger
 //     primes from a per-block list (at most sixteen multiples of p^2 per
 //     prime in a block of up to 2^30 y).
@@ -649,12 +649,12 @@ struct T2Args {
     uint64_t y1;
     uint32_t len;          // <= 2^30
     uint32_t np;           // primes used (all p <= P)
-    uint32_t np_lane;      // [4, np_lane): 11 <= p < 512, a warp per prime
+    uint32_t np_lane;      // [4, np_lane): 11 <= p < 1024, a warp per prime
     uint32_t np_list;      // [np_list, np): p >= 8192, squares from the block's list
     float thr_half;        // log2 P
     const uint4 *pq;       // {p, m32(p), m32(p^2) or 0, s(p) | s(p^2) << 8 | w2(p) << 16}
-    const uint4 *rec;      // per block, p >= 512: {p, m32(p), y1 mod p, s(p) | w2(p) << 8}
-    const uint2 *rec2;     // per block, 512 <= p < 8192: {y1 mod p^2 | s(p^2) << 26, m32(p^2)}
+    const uint4 *rec;      // per block, p >= 1024: {p, m32(p), y1 mod p, s(p) | w2(p) << 8}
+    const uint2 *rec2;     // per block, 1024 <= p < 8192: {y1 mod p^2 | s(p^2) << 26, m32(p^2)}
     const uint32_t *r;     // y1 mod p
     const uint64_t *r2;    // y1 mod p^2
     const uint4 *pat;      // 16 phase copies of the 2, 3, 5, 7 pattern
@@ -669,9 +669,11 @@ struct T2Args {
     uint32_t *err;         // kErrTimeout / kErrBucket
 };
 
-constexpr uint32_t kT2JobsMax = 128;          // descriptor jobs (93: the primes 11 .. 509)
+constexpr uint32_t kT2JobsMax = 192;          // descriptor jobs (168: the primes 11 .. 1021)
 constexpr uint32_t kPat2Len = 142416;         // >= 44100 + 98304, multiple of 16
-constexpr uint32_t kT2LaneMin = 512;          // primes from here: a lane per prime
+constexpr uint32_t kT2LaneMin = 1024;         // primes from here: a lane per prime
+// a lane prime marks at most one multiple of its square per tile (98304 y)
+static_assert(kT2LaneMin * kT2LaneMin > 98304u, "lane primes need p^2 above the tile");
 constexpr uint32_t kT2ListMin = 8192;         // primes from here: squares from the list
 constexpr uint64_t kT2MinTile = 65536;        // smallest tile (square-list scratch)
 // Status bit: a bucket or a square list overflowed its capacity.
@@ -715,7 +717,7 @@ __global__ void t2_block_prep_kernel(uint64_t y1, uint32_t np, const uint4 *__re
 
 // Descriptor job i of a tile of TILE y: {first multiple, tl, p | w2 << 16,
 // first multiple of p^2 or kNone when p^2 > TILE}; *single = the one multiple
-// of p^2 in the tile when p^2 > TILE.  Jobs: the primes 11 <= p < 512 in
+// of p^2 in the tile when p^2 > TILE.  Jobs: the primes 11 <= p < 1024 in
 // order (index 4 + i), largest work first.
 template <int TILE>
 __device__ __forceinline__ uint4 t2_desc(const T2Args &a, uint32_t i, uint32_t a0,
@@ -767,7 +769,7 @@ __device__ __forceinline__ void t2_desc_job(uint4 d, uint32_t *w, uint32_t lane)
     }
 }
 
-// One prime p >= 512 over the whole tile (one lane): its weights, and its
+// One prime p >= 1024 over the whole tile (one lane): its weights, and its
 // square when p < 8192 (p^2 > tile: at most one multiple).  Its per-block
 // record q = {p, m32(p), y1 mod p, s(p) | w2(p) << 8} and, below 8192,
 // e = {y1 mod p^2 | s(p^2) << 26, m32(p^2)} (see t2_block_prep_kernel).
@@ -780,7 +782,7 @@ __device__ __forceinline__ void t2_lane_prime(uint4 q, uint2 e, uint32_t *w, uin
     const uint32_t v = q.z + a0;  // < 2^31
     const uint32_t rem = v - div_magic32(v, q.y, q.w & 255u) * p;
     uint32_t yo = rem ? p - rem : 0u;
-    if (p < (uint32_t)TILE / 9u) {
+    if (p < (uint32_t)TILE / 3u) {
         // four hits per round: p is odd, so the four byte positions of
         // yo, yo+p, yo+2p, yo+3p repeat every 4p
         const uint32_t w0 = wt << ((yo & 3u) << 3);
@@ -1005,8 +1007,8 @@ __global__ void __launch_bounds__(THREADS, MINB) mu_sieve_t2_kernel(T2Args a)
     const uint64_t t1 = a.y1 + a0;
     const uint32_t tl = min(a.len - a0, (uint32_t)TILE);
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    const uint32_t jd = a.np_lane - 4;  // descriptor jobs: primes 11 <= p < 512
-    const uint32_t jobs = jd + (a.np - a.np_lane + 63u) / 64u;
+    const uint32_t jd = a.np_lane - 4;  // descriptor jobs: primes 11 <= p < 1024
+    const uint32_t jobs = jd + (a.np - a.np_lane + 127u) / 128u;
     const uint32_t nsq = min(a.sqcnt[blockIdx.x], a.sqcap);
 
     uint32_t single = kNone;
@@ -1050,9 +1052,9 @@ __global__ void __launch_bounds__(THREADS, MINB) mu_sieve_t2_kernel(T2Args a)
     }
 
     // jobs, largest first, handed out through a shared counter: descriptor
-    // jobs (a warp over the multiples of one prime), then 64 primes >= 512 at
-    // a time (a lane takes primes i and 63 - i of the job, so the lanes' hit
-    // counts even out)
+    // jobs (a warp over the multiples of one prime), then 128 primes >= 1024
+    // at a time (a lane takes primes i and 63 - i of each half of the job, so
+    // the lanes' hit counts even out)
     for (;;) {
         uint32_t job = 0;
         if (lane == 0)
@@ -1063,7 +1065,8 @@ __global__ void __launch_bounds__(THREADS, MINB) mu_sieve_t2_kernel(T2Args a)
         if (job < jd) {
             t2_desc_job(s_jd[job], w, lane);
         } else {
-            const uint32_t b0 = a.np_lane + (job - jd) * 64u;
+            for (uint32_t hb = 0; hb < 128u; hb += 64u) {
+            const uint32_t b0 = a.np_lane + (job - jd) * 128u + hb;
             const uint32_t t0 = b0 + lane, t1p = b0 + 63u - lane;
             uint4 q0 = make_uint4(0, 0, 0, 0), q1 = q0;
             uint2 e0 = make_uint2(0, 0), e1 = e0;
@@ -1081,6 +1084,7 @@ __global__ void __launch_bounds__(THREADS, MINB) mu_sieve_t2_kernel(T2Args a)
                 t2_lane_prime<TILE>(q0, e0, w, a0, tl);
             if (t1p < a.np)
                 t2_lane_prime<TILE>(q1, e1, w, a0, tl);
+            }
         }
     }
     __syncthreads();
