@@ -568,7 +568,7 @@ def run_native(args, world, rank, local):
             # executes one quotient per squarefree y below the dense cut-off and
             # one per gathered j above it, less the gathered terms entry 2x takes
             # from entry x's even j (floor(floor(n/x)/2j) = floor(floor(n/2x)/j)):
-            "terms_executed_per_step": SIX_OVER_PI2 * stats["dense_y"] + stats["gather_j_exec"],
+            "terms_executed_per_step": dense_evaluated(stats) + stats["gather_j_exec"],
             "gathered_terms_shared_per_step": stats["gather_j"] - stats["gather_j_exec"],
             "phases_ms": {k: round(v, 3) for k, v in phases.items()},
             "y_sieved_per_s": stats["y_sieved"] * world / (ms_max / 1e3),
@@ -676,18 +676,25 @@ def window_measure(stream):
 #     class's main kernel (share of cycles a scheduler issued an instruction);
 #   pipe: the busiest pipe of that kernel and its share of active cycles.
 NCU = {
-    "mu_sieve": {"kernel": "mu_sieve_t2_kernel", "dram_bytes_per_step": 72.9e9,
-                 "issue_active": 0.605, "pipe": ("alu", 0.385)},
-    "update_dense": {"kernel": "dense_update_kernel", "dram_bytes_per_step": 0.872e9,
-                     "issue_active": 0.485, "pipe": ("fmaheavy", 0.874)},
-    "update_gathered": {"kernel": "gather_tile_kernel", "dram_bytes_per_step": 19.25e9,
-                        "issue_active": 0.886, "pipe": ("alu", 0.619)},
+    "mu_sieve": {"kernel": "mu_sieve_t2_kernel", "dram_bytes_per_step": 72.3e9,
+                 "issue_active": 0.663, "pipe": ("alu", 0.432)},
+    "update_dense": {"kernel": "dense_update_kernel", "dram_bytes_per_step": 0.87e9,
+                     "issue_active": 0.446, "pipe": ("fmaheavy", 0.799)},
+    "update_gathered": {"kernel": "gather_tile_kernel", "dram_bytes_per_step": 13.9e9,
+                        "issue_active": 0.830, "pipe": ("fmaheavy", 0.668)},
 }
 # Issue slots of the chip: 152 SMs x 4 schedulers x one warp instruction per
 # clock at the maximum SM clock.
 ISSUE_PEAK_WARP_INSTR_PER_S = 152 * 4 * 2070e6
 
 SIX_OVER_PI2 = 6.0 / math.pi ** 2
+
+
+def dense_evaluated(stats):
+    """Squarefree y the dense kernel evaluates: (6/pi^2) of the summed dense
+    y-ranges, less the odd squarefree y (8/pi^2 of the odd y) that entries 2x
+    take from entries x (mu(y) floor(floor(n/2x)/y) = -mu(2y) floor(floor(n/x)/2y))."""
+    return SIX_OVER_PI2 * stats["dense_y"] - (4.0 / 3.0) * SIX_OVER_PI2 * stats["dense_odd_skip"]
 
 
 def rooflines(phases, stats, peaks, nblocks, ipk):
@@ -702,8 +709,7 @@ def rooflines(phases, stats, peaks, nblocks, ipk):
     ncu issue-active share of the class's main kernel and its busiest pipe
     (NCU above), against the chip's issue slots.
       update_dense: the update's inner step acc += mulhi64(m, 2k) >> l, in
-        terms/s.  Algorithmic terms: squarefree y of the dense ranges
-        ((6/pi^2) x the summed dense y-range).
+        terms/s.  Units: squarefree y the kernel evaluates (dense_evaluated).
       update_gathered: one term per gathered j evaluated (entry 2x takes
         part of its terms from entry x's even j, so fewer than the method's
         gathered terms), against the faster of that step and the
@@ -720,7 +726,7 @@ def rooflines(phases, stats, peaks, nblocks, ipk):
     work = {
         "mu_sieve": (stats["sieve_updates"] + 2.0 * stats["y_sieved"], alu_peak, "T int-op/s",
                      "inner-step probe: LOP3+IADD3 chains on all SMs, 2 ops per pair"),
-        "update_dense": (SIX_OVER_PI2 * stats["dense_y"], mulhi_peak, "T mulhi-terms/s",
+        "update_dense": (dense_evaluated(stats), mulhi_peak, "T mulhi-terms/s",
                          "inner-step probe: acc += mulhi64(m,2k) >> l chains on all SMs"),
         "update_gathered": (float(stats["gather_j_exec"]), gather_peak, "T terms/s",
                             "inner-step probe: the faster of the mulhi64 step and the "

@@ -295,6 +295,13 @@ typedef struct {
                              even j (floor(floor(n/x)/2j') =
                              floor(floor(n/2x)/j')), so these are fewer
                              than gather_j                                  */
+    uint64_t dense_odd_skip; /* odd y left out of the dense sums, summed over
+                             entries: entry 2x takes its odd-y terms up to
+                             half of entry x's cut-off from entry x's
+                             even-y terms (mu(y) floor(floor(n/2x)/y) =
+                             -mu(2y) floor(floor(n/x)/2y)); the squarefree
+                             ones among them, about 8/pi^2 of these, are
+                             not evaluated                                  */
 } mertens_run_stats;
 
 /* Enables (1) or disables (0) per-phase events for later runs of `plan`

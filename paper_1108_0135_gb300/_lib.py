@@ -44,7 +44,7 @@ class mertens_run_stats(ctypes.Structure):
                 ("dense_y", ctypes.c_uint64), ("gather_j", ctypes.c_uint64),
                 ("sieve_updates", ctypes.c_double),
                 ("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64),
-                ("gather_j_exec", ctypes.c_uint64)]
+                ("gather_j_exec", ctypes.c_uint64), ("dense_odd_skip", ctypes.c_uint64)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)

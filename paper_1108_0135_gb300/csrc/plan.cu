@@ -8,6 +8,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <thread>
 #include <vector>
 
 #include "../../include/libmertens.h"
@@ -16,6 +17,36 @@
 #include "update.h"
 
 namespace mert {
+
+// Runs f(lo, hi) over [0, n) in contiguous pieces of at least min_piece on up
+// to 16 host threads (host planning only; f must not throw).  Falls back to
+// the calling thread alone when a thread cannot be started.
+template <typename F>
+static void parallel_for(size_t n, size_t min_piece, const F &f)
+{
+    const unsigned hw = std::thread::hardware_concurrency();
+    size_t nt = std::min<size_t>(hw ? hw : 1, 16);
+    nt = std::min(nt, std::max<size_t>(1, n / std::max<size_t>(min_piece, 1)));
+    if (nt <= 1) {
+        f((size_t)0, n);
+        return;
+    }
+    const size_t step = (n + nt - 1) / nt;
+    std::vector<std::thread> th;
+    size_t done_from = step;  // pieces from here on not started on a thread
+    try {
+        for (size_t lo = step; lo < n; lo += step) {
+            th.emplace_back([&f, lo, n, step]() { f(lo, std::min(n, lo + step)); });
+            done_from = lo + step;
+        }
+    } catch (...) {
+    }
+    f((size_t)0, std::min(n, step));
+    if (done_from < n)
+        f(done_from, n);
+    for (auto &t : th)
+        t.join();
+}
 
 // ---------------------------------------------------------------------------
 // Errors and allocation.
@@ -194,6 +225,7 @@ struct mertens_plan_s {
     uint64_t *dK = nullptr, *dJLO = nullptr, *dJC0 = nullptr, *dJCUR = nullptr, *dYCE = nullptr;
     uint32_t *dEMIT = nullptr;
     uint64_t gather_j_exec = 0;  // gathered terms evaluated (after sharing)
+    uint64_t dense_odd_skip = 0; // odd y left out of dense sums (taken from entries x/2)
     uint64_t *dS = nullptr, *dR = nullptr;
     // chunks of the global gather's heavy entries, per block (qcap records)
     uint4 *dqueue = nullptr;
@@ -578,15 +610,35 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
         std::vector<uint64_t> S_(64), VH(64);
         std::vector<uint8_t> WD(64);
         const u128 wide_from = wide_threshold();
+        // per entry, on host threads: k = floor(n/x) (0 for a two-word entry),
+        // s = floor(sqrt(k)) and the top of its valid dense cut-offs
+        std::vector<uint64_t> Kx(X), Sx(X), VHx(X), JLx(X);
+        parallel_for(X, 4096, [&](size_t lo, size_t hi) {
+            for (size_t i = lo; i < hi; ++i) {
+                const uint64_t x = i + 1;
+                const u128 k128 = nn / x;
+                JLx[i] = X / x + 1;  // = floor(k/u) + 1
+                if (k128 >= wide_from) {
+                    Kx[i] = Sx[i] = VHx[i] = 0;
+                    continue;
+                }
+                const uint64_t k = (uint64_t)k128, sq = isqrt64(k), jlo = JLx[i];
+                Kx[i] = k;
+                Sx[i] = sq;
+                // valid dense cut-offs: [s, floor(k/jlo) - 1] when the entry
+                // has gathered terms, else exactly s
+                VHx[i] = (jlo <= k / (sq + 1)) ? (k / jlo - 1) : sq;
+            }
+        });
         for (uint64_t x0 = 1; x0 <= X; x0 += 64) {
             const uint32_t cnt = (uint32_t)std::min<uint64_t>(64, X - x0 + 1);
             uint64_t lo = 0, hi = UINT64_MAX, kf = 0;
             bool any_wide = false;
             for (uint32_t t = 0; t < cnt; ++t) {
                 const uint64_t x = x0 + t;
-                const u128 k128 = nn / x;
-                const uint64_t jlo = X / x + 1;  // = floor(k/u) + 1
-                if (k128 >= wide_from) {
+                const uint64_t jlo = JLx[x - 1];
+                if (Kx[x - 1] == 0) {
+                    const u128 k128 = nn / x;
                     // two-word entry: its own kernel; k = 0 (no terms) here
                     WideEntry W;
                     W.k_lo = (uint64_t)k128;
@@ -611,11 +663,7 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
                     JLO.push_back(1);
                     continue;
                 }
-                const uint64_t k = (uint64_t)k128, s = isqrt64(k);
-                const uint64_t jhi = k / (s + 1);
-                // valid dense cut-offs: [s, floor(k/jlo) - 1] when the entry
-                // has gathered terms, else exactly s
-                const uint64_t vh = (jlo <= jhi) ? (k / jlo - 1) : s;
+                const uint64_t k = Kx[x - 1], s = Sx[x - 1], vh = VHx[x - 1];
                 S_[t] = s;
                 VH[t] = vh;
                 WD[t] = 0;
@@ -624,8 +672,6 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
                 lo = std::max(lo, s);
                 hi = std::min(hi, vh);
                 d += s;
-                if (jhi >= jlo)
-                    g += jhi - jlo + 1;
                 K.push_back(k);
                 JLO.push_back(jlo);
             }
@@ -676,24 +722,50 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
                     groups.push_back(H);
                 }
             }
-            for (uint32_t t = 0; t < cnt; ++t) {
-                const size_t e = G.first + t;
-                if (WD[t]) {
-                    JC0.push_back(0);
-                    continue;
+        }
+        {
+            // per entry, on host threads: the top of the gathered range
+            // JC0 = floor(k/(yc+1)), the largest y it needs, and the totals
+            const size_t o = p->off.back();
+            JC0.resize(o + X, 0);
+            struct Part {
+                uint64_t ymq = 0, ydense = 0, jmax = 0, dense_y = 0, gather_j = 0, g = 0;
+            };
+            const size_t npart = 64;
+            std::vector<Part> parts(npart);
+            const size_t per = (X + npart - 1) / npart;
+            parallel_for(npart, 1, [&](size_t lo, size_t hi) {
+                for (size_t q = lo; q < hi; ++q) {
+                    Part &P = parts[q];
+                    for (size_t i = q * per; i < std::min<size_t>(X, (q + 1) * per); ++i) {
+                        const size_t e = o + i;
+                        const uint64_t k = K[e];
+                        if (k == 0)
+                            continue;  // two-word entry (counted with the others above)
+                        const uint64_t yc = YCE[e], jc0 = k / (yc + 1);
+                        JC0[e] = jc0;
+                        uint64_t need = yc;
+                        if (JLO[e] <= jc0)
+                            need = std::max(need, k / JLO[e]);
+                        P.ymq = std::max(P.ymq, need);
+                        P.ydense = std::max(P.ydense, yc);
+                        P.jmax = std::max(P.jmax, jc0);
+                        P.dense_y += yc;
+                        if (jc0 >= JLO[e])
+                            P.gather_j += jc0 - JLO[e] + 1;
+                        const uint64_t jhi = k / (Sx[i] + 1);  // the split form's t = s + 1
+                        if (jhi >= JLO[e])
+                            P.g += jhi - JLO[e] + 1;
+                    }
                 }
-                const uint64_t k = K[e], yc = YCE[e];
-                const uint64_t jc0 = k / (yc + 1);
-                JC0.push_back(jc0);
-                uint64_t need = yc;
-                if (JLO[e] <= jc0)
-                    need = std::max(need, k / JLO[e]);
-                ymq = std::max(ymq, need);
-                p->ydense = std::max(p->ydense, yc);
-                p->jmax = std::max(p->jmax, jc0);
-                p->dense_y += yc;
-                if (jc0 >= JLO[e])
-                    p->gather_j += jc0 - JLO[e] + 1;
+            });
+            for (const Part &P : parts) {
+                ymq = std::max(ymq, P.ymq);
+                p->ydense = std::max(p->ydense, P.ydense);
+                p->jmax = std::max(p->jmax, P.jmax);
+                p->dense_y += P.dense_y;
+                p->gather_j += P.gather_j;
+                g += P.g;
             }
         }
         // ---- the dense form's terms shared between entries x and 2x ----
@@ -724,6 +796,7 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
                 if (!ok)
                     continue;
                 R.olo = b;
+                p->dense_odd_skip += (b + 1) / 2 * (uint64_t)R.count;
                 for (uint32_t t = 0; t < R.count; ++t) {
                     const uint64_t xs = 32 * M + 1 + t;       // source x
                     const uint64_t o = xs - (64 * (M / 2) + 1);  // offset in its block
@@ -916,7 +989,6 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
     }
     std::vector<GatherTile> gtiles;
     std::vector<GatherItem> gitems;
-    std::vector<std::pair<uint64_t, uint64_t>> ranges;
     // Blocks above the tile range: tiles over the whole block for the
     // entries with k >= kt_fac y1^2 / kGatherTile (about kt_fac terms or more
     // per tile; a prefix of each target's entries), when they have at least
@@ -950,76 +1022,94 @@ static int plan_create(mertens_plan_t *out, const mertens_u128 *n, size_t count,
             }
         }
         p->ktile.push_back(kt);
-        for (uint64_t t1 = y1; t1 <= end; t1 += kGatherTile) {
-            const uint64_t t2 = std::min(t1 + kGatherTile - 1, end);
-            GatherTile T;
-            T.t1 = t1;
-            T.len = (uint32_t)(t2 - t1 + 1);
-            T.m1 = magic_of(t1);
-            T.l1 = magic_shift(t1);
-            T.m2 = magic_of(t2 + 1);
-            T.l2 = magic_shift(t2 + 1);
-            T.pad = 0;
-            const uint32_t ti = (uint32_t)gtiles.size();
-            // entries that can have terms here: per target the suffix whose
-            // cut-off lies below t2 (found on the running minimum); suffixes
-            // of consecutive targets separated by short gaps are merged (an
-            // entry outside its suffix simply has no terms in the tile)
-            ranges.clear();
-            for (size_t i = 0; i < count; ++i) {
-                const uint64_t o = p->off[i], X = p->X[i];
-                uint64_t lo = 0, hi = X;  // first x index with ycmin < t2
-                while (lo < hi) {
-                    const uint64_t mid = (lo + hi) / 2;
-                    if (ycmin[o + mid] < t2)
-                        hi = mid;
-                    else
-                        lo = mid + 1;
-                }
-                // above the tile range only the prefix with k >= kt
-                uint64_t top = X;
-                if (kt != UINT64_MAX) {
-                    uint64_t a = 0, z = X;  // first x index with k < kt
-                    while (a < z) {
-                        const uint64_t mid = (a + z) / 2;
-                        if (K[o + mid] >= kt || K[o + mid] == 0)
-                            a = mid + 1;
+        // the block's tiles on host threads, then appended in order (a tile
+        // is kept when some entry range can have terms in it)
+        const uint64_t ntile = y1 <= end ? (end - y1) / kGatherTile + 1 : 0;
+        std::vector<GatherTile> btiles(ntile);
+        std::vector<std::vector<GatherItem>> bitems(ntile);
+        parallel_for(ntile, 64, [&](size_t qlo, size_t qhi) {
+            std::vector<std::pair<uint64_t, uint64_t>> ranges;
+            for (size_t q = qlo; q < qhi; ++q) {
+                const uint64_t t1 = y1 + q * kGatherTile;
+                const uint64_t t2 = std::min(t1 + kGatherTile - 1, end);
+                GatherTile &T = btiles[q];
+                T.t1 = t1;
+                T.len = (uint32_t)(t2 - t1 + 1);
+                T.m1 = magic_of(t1);
+                T.l1 = magic_shift(t1);
+                T.m2 = magic_of(t2 + 1);
+                T.l2 = magic_shift(t2 + 1);
+                T.pad = 0;
+                // entries that can have terms here: per target the suffix
+                // whose cut-off lies below t2 (found on the running minimum);
+                // suffixes of consecutive targets separated by short gaps are
+                // merged (an entry outside its suffix simply has no terms in
+                // the tile)
+                ranges.clear();
+                for (size_t i = 0; i < count; ++i) {
+                    const uint64_t o = p->off[i], X = p->X[i];
+                    uint64_t lo = 0, hi = X;  // first x index with ycmin < t2
+                    while (lo < hi) {
+                        const uint64_t mid = (lo + hi) / 2;
+                        if (ycmin[o + mid] < t2)
+                            hi = mid;
                         else
-                            z = mid;
+                            lo = mid + 1;
                     }
-                    top = a;
-                }
-                if (lo >= top)
-                    continue;
-                if (!ranges.empty() && o + lo <= ranges.back().second + 4096 &&
-                    kt == UINT64_MAX)
-                    ranges.back().second = o + top;
-                else
-                    ranges.push_back({o + lo, o + top});
-            }
-            // work of entries [f, g): about one range check each plus
-            // sum k * len / t1^2 gathered terms; items of ~kItemWork
-            const double per_k = (double)T.len / ((double)t1 * (double)t1);
-            for (const auto &rg : ranges) {
-                for (uint64_t f = rg.first; f < rg.second;) {
-                    uint64_t g = std::min<uint64_t>(f + 1024, rg.second);
-                    while (g < rg.second) {
-                        const double work = (double)(g - f) + per_k * (kpre[g] - kpre[f]);
-                        if (work >= kItemWork)
-                            break;
-                        g = std::min<uint64_t>(g + 1024, rg.second);
+                    // above the tile range only the prefix with k >= kt
+                    uint64_t top = X;
+                    if (kt != UINT64_MAX) {
+                        uint64_t a = 0, z = X;  // first x index with k < kt
+                        while (a < z) {
+                            const uint64_t mid = (a + z) / 2;
+                            if (K[o + mid] >= kt || K[o + mid] == 0)
+                                a = mid + 1;
+                            else
+                                z = mid;
+                        }
+                        top = a;
                     }
-                    GatherItem it;
-                    it.tile = ti;
-                    it.e0 = (uint32_t)f;
-                    it.e1 = (uint32_t)g;
-                    it.pad = 0;
-                    gitems.push_back(it);
-                    f = g;
+                    if (lo >= top)
+                        continue;
+                    if (!ranges.empty() && o + lo <= ranges.back().second + 4096 &&
+                        kt == UINT64_MAX)
+                        ranges.back().second = o + top;
+                    else
+                        ranges.push_back({o + lo, o + top});
+                }
+                // work of entries [f, g): about one range check each plus
+                // sum k * len / t1^2 gathered terms; items of ~kItemWork
+                const double per_k = (double)T.len / ((double)t1 * (double)t1);
+                for (const auto &rg : ranges) {
+                    for (uint64_t f = rg.first; f < rg.second;) {
+                        uint64_t g = std::min<uint64_t>(f + 1024, rg.second);
+                        while (g < rg.second) {
+                            const double work =
+                                (double)(g - f) + per_k * (kpre[g] - kpre[f]);
+                            if (work >= kItemWork)
+                                break;
+                            g = std::min<uint64_t>(g + 1024, rg.second);
+                        }
+                        GatherItem it;
+                        it.tile = 0;  // set when the tile is appended
+                        it.e0 = (uint32_t)f;
+                        it.e1 = (uint32_t)g;
+                        it.pad = 0;
+                        bitems[q].push_back(it);
+                        f = g;
+                    }
                 }
             }
-            if (!ranges.empty())
-                gtiles.push_back(T);
+        });
+        for (size_t q = 0; q < ntile; ++q) {
+            if (bitems[q].empty())
+                continue;
+            const uint32_t ti = (uint32_t)gtiles.size();
+            gtiles.push_back(btiles[q]);
+            for (GatherItem it : bitems[q]) {
+                it.tile = ti;
+                gitems.push_back(it);
+            }
         }
     }
     p->gblk.push_back((uint32_t)gitems.size());
@@ -2050,6 +2140,7 @@ int mertens_run_stats_get(mertens_plan_t p, mertens_run_stats *st)
     st->dense_y = p->dense_y;
     st->gather_j = p->gather_j;
     st->gather_j_exec = p->gather_j_exec;
+    st->dense_odd_skip = p->dense_odd_skip;
     st->sieve_updates = p->sieve_updates;
     st->h2d_bytes = p->h2d_bytes;
     st->d2h_bytes = p->d2h_bytes;
