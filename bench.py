@@ -677,7 +677,7 @@ def window_measure(stream):
 #   pipe: the busiest pipe of that kernel and its share of active cycles.
 NCU = {
     "mu_sieve": {"kernel": "mu_sieve_t2_kernel", "dram_bytes_per_step": 72.3e9,
-                 "issue_active": 0.663, "pipe": ("alu", 0.432)},
+                 "issue_active": 0.666, "pipe": ("alu", 0.436)},
     "update_dense": {"kernel": "dense_update_kernel", "dram_bytes_per_step": 0.87e9,
                      "issue_active": 0.446, "pipe": ("fmaheavy", 0.799)},
     "update_gathered": {"kernel": "gather_tile_kernel", "dram_bytes_per_step": 13.9e9,

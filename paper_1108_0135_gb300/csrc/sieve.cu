@@ -640,7 +640,7 @@ __global__ void __launch_bounds__(kSieveThreads, 1) mu_sieve_byte_kernel(ByteArg
 //   * primes 11 <= p < 1024: a warp over the multiples of one prime, largest
 //     jobs first;
 //   * primes p >= 1024: a lane per prime, four per lane, the hits of primes
-//     below a third of the tile four at a time with loop-invariant shifted
+//     below half the tile four at a time with loop-invariant shifted
 //     weights; the square of a prime below 8192 per lane, those of larger
 //     primes from a per-block list (at most sixteen multiples of p^2 per
 //     prime in a block of up to 2^30 y).
@@ -782,7 +782,7 @@ __device__ __forceinline__ void t2_lane_prime(uint4 q, uint2 e, uint32_t *w, uin
     const uint32_t v = q.z + a0;  // < 2^31
     const uint32_t rem = v - div_magic32(v, q.y, q.w & 255u) * p;
     uint32_t yo = rem ? p - rem : 0u;
-    if (p < (uint32_t)TILE / 3u) {
+    if (p < (uint32_t)TILE / 2u) {
         // four hits per round: p is odd, so the four byte positions of
         // yo, yo+p, yo+2p, yo+3p repeat every 4p
         const uint32_t w0 = wt << ((yo & 3u) << 3);
