@@ -124,3 +124,40 @@ def test_plan_rejects_empty_batch():
     h = ctypes.c_void_p()
     rc = lib.mertens_plan(ctypes.byref(h), None, 0, pm._lib.u128(0), 0)
     assert rc == pm.MERTENS_EINVAL and not h.value
+
+
+def header_structs():
+    """{typedef name: [(C type, field name), ...]} of the header's structs."""
+    text = open(os.path.join(ROOT, "include", "libmertens.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    out = {}
+    for body, name in re.findall(r"typedef struct\s*\{(.*?)\}\s*([a-z_0-9]+)\s*;", text, flags=re.S):
+        fields = []
+        for decl in body.split(";"):
+            decl = decl.strip()
+            if not decl:
+                continue
+            ctype, rest = decl.split(None, 1)
+            fields += [(ctype, f.strip()) for f in rest.split(",")]
+        out[name] = fields
+    return out
+
+
+def test_ctypes_structs_match_the_header():
+    """Every struct the binding passes by pointer has the header's fields, in
+    its order and with its C types (a mismatch would shift every later
+    field)."""
+    cmap = {"uint64_t": ctypes.c_uint64, "int64_t": ctypes.c_int64, "uint32_t": ctypes.c_uint32,
+            "int32_t": ctypes.c_int32, "int": ctypes.c_int, "double": ctypes.c_double,
+            "mertens_u128": pm._lib.mertens_u128}
+    structs = header_structs()
+    checked = 0
+    for name, fields in structs.items():
+        cls = getattr(pm._lib, name, None)
+        if cls is None:
+            continue
+        got = [(f, t) for f, t in cls._fields_]
+        want = [(f, cmap[t]) for t, f in fields]
+        assert got == want, name
+        checked += 1
+    assert checked >= 6
